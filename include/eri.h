@@ -1,0 +1,152 @@
+/*
+ * liberi: integral-direct Coulomb / exchange (J/K) builds over contracted
+ * Cartesian Gaussian shells up to g, evaluated by Rys quadrature on one
+ * NVIDIA GB300 (sm_103a).  Method: arXiv 2407.09700 (GPU4PySCF), Secs. 2-3.
+ *
+ * All entry points are plain C.  Status codes are returned, nothing aborts and
+ * no exception crosses the boundary; on failure eri_last_error() gives a
+ * message (thread-local, valid until the next call on the same thread).
+ *
+ * Conventions shared by every entry point:
+ *   - atomic units (Bohr); coordinates row-major [natm][3];
+ *   - Cartesian components of a shell in x-descending order
+ *     (for lx = l..0, for ly = l-lx..0: xx, xy, xz, yy, yz, zz for d);
+ *   - basis functions numbered shell by shell in the order given;
+ *   - contraction coefficients, when normalise = 1, get the radial primitive
+ *     norm (2a/pi)^(3/4) (4a)^(l/2) / sqrt((2l-1)!!) and the contracted shell is
+ *     rescaled so its x^l component has unit self-overlap (Eqs. 2, 4-5, Sec. 2;
+ *     the paper leaves the convention open);
+ *   - matrices are row-major [nD][nbf][nbf] FP64.
+ */
+#ifndef ERI_H
+#define ERI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  ERI_OK = 0,
+  ERI_ERR_ARG = 1,            /* bad argument (null pointer, size, index, option) */
+  ERI_ERR_BASIS = 2,          /* malformed basis: nprim < 1, non-finite or non-positive exponent, bad atom index */
+  ERI_ERR_OOM = 3,            /* device or host allocation failed; the plan is left unchanged */
+  ERI_ERR_CUDA = 4,           /* a CUDA runtime call failed; message in eri_last_error() */
+  ERI_ERR_NO_DEVICE = 5,      /* no CUDA device is visible */
+  ERI_ERR_TIMEOUT = 6,        /* a bounded wait gave up */
+  ERI_ERR_UNSUPPORTED_L = 7   /* angular momentum above g (l > 4); Sec. 3 stops at g */
+} eri_status;
+
+enum { ERI_FP64 = 0, ERI_MIXED = 1 };
+enum { ERI_WANT_J = 1, ERI_WANT_K = 2 };
+
+typedef struct eri_plan eri_plan;
+
+/* Basis set: all arrays on the host, read during eri_plan_create only. */
+typedef struct {
+  int natm;
+  const double* coords;      /* [natm][3], Bohr */
+  int nshell;
+  const int* shell_atom;     /* [nshell] atom of each shell */
+  const int* shell_l;        /* [nshell] angular momentum, 0..4 */
+  const int* shell_nprim;    /* [nshell] contraction depth K >= 1 */
+  const int* shell_off;      /* [nshell] first primitive of the shell in exps / coefs */
+  const double* exps;        /* primitive exponents, > 0 */
+  const double* coefs;       /* contraction coefficients (raw if normalise = 1) */
+  int normalise;             /* 1: apply the normalisation above; 0: use coefs as given */
+} eri_basis;
+
+typedef struct {
+  double screen_thresh;      /* tau of Eqs. 6-9 (Sec. 3); shell pairs with Q <= tau are dropped */
+  int precision;             /* ERI_FP64 (all FP64) or ERI_MIXED */
+  double mixed_thresh;       /* ERI_MIXED: quartets whose Schwarz x density bound is <= this run in FP32 */
+  int max_nd;                /* largest nD an eri_jk call may pass (>= 1) */
+} eri_opts;
+
+/* Counters of the last eri_jk call on the plan (filled after that call's stream completes). */
+typedef struct {
+  long long quartets_candidate;   /* unique shell quartets formed from the kept shell pairs */
+  long long quartets_computed;    /* unique shell quartets that passed the screening test */
+  long long prim_quartets;        /* primitive quartets evaluated */
+  long long quartets_fp32;        /* of quartets_computed, those run in FP32 (ERI_MIXED) */
+  double model_flops;             /* FP64+FP32 arithmetic of the Rys kernels, counted per class */
+  int npairs_total;               /* shell pairs i >= j */
+  int npairs_kept;                /* shell pairs with Q > tau */
+  int nclasses_launched;
+} eri_stats;
+
+/*
+ * Create a plan: validates and normalises the basis, forms every shell pair
+ * (i >= j) with its primitive-pair data (Gaussian product theorem, Eq. 2),
+ * computes the Cauchy-Schwarz factors Q_ij = max |(ab|ab)|^(1/2) of Eq. 7 on
+ * the GPU, keeps pairs with Q > tau and groups them by angular-momentum class
+ * (Alg. 1 of Sec. 3).  Synchronous.  The plan owns all its device memory.
+ * cuda_stream: a cudaStream_t or NULL for the default stream.
+ * Errors: ERI_ERR_ARG (null pointers, tau < 0, max_nd < 1), ERI_ERR_BASIS,
+ * ERI_ERR_UNSUPPORTED_L, ERI_ERR_NO_DEVICE, ERI_ERR_OOM, ERI_ERR_CUDA.
+ */
+eri_status eri_plan_create(const eri_basis* basis, const eri_opts* opts, void* cuda_stream,
+                           eri_plan** out);
+
+/* Free a plan and its device memory (synchronises the device first).  NULL is accepted. */
+eri_status eri_plan_destroy(eri_plan* plan);
+
+/* Number of Cartesian basis functions, or -1 for a NULL plan. */
+int eri_plan_nbf(const eri_plan* plan);
+
+/*
+ * Coulomb and exchange matrices (Sec. 3, Algs. 1-3):
+ *   J_ij = sum_kl (ij|kl) D_kl,   K_ik = sum_jl (ij|kl) D_jl,
+ * for nD symmetric densities, using the 8-fold permutation symmetry of (ij|kl)
+ * and the screening of Eqs. 7-9: a unique shell quartet is evaluated when
+ * Q_ij * Q_kl * max|D| over its six cross blocks >= tau.
+ * D, J, K: DEVICE pointers, contiguous [nD][nbf][nbf] FP64, 1 <= nD <= max_nd.
+ * D must be symmetric (not checked).  J and K are overwritten, never
+ * accumulated.  flags: ERI_WANT_J | ERI_WANT_K (an unwanted output may be
+ * NULL and is not touched).  Asynchronous on cuda_stream; the plan's scratch is
+ * reused by every call, so calls on one plan must not overlap on the GPU.
+ */
+eri_status eri_jk(eri_plan* plan, const double* D, int nD, double* J, double* K, int flags,
+                  void* cuda_stream);
+
+/*
+ * Same as eri_jk, with D, J and K in HOST memory: copies D to the device,
+ * builds J/K and copies them back.  Synchronous.
+ */
+eri_status eri_jk_host(eri_plan* plan, const double* D, int nD, double* J, double* K, int flags,
+                       void* cuda_stream);
+
+/*
+ * One contracted shell quartet (ij|kl) by Rys quadrature (Eq. 1 contracted by
+ * Eq. 5), no screening: writes n_i*n_j*n_k*n_l FP64 values in (i,j,k,l)
+ * row-major Cartesian order to out (HOST memory).  Synchronous.
+ * Errors: ERI_ERR_ARG for a shell index outside [0, nshell).
+ */
+eri_status eri_shell_quartet(eri_plan* plan, int i, int j, int k, int l, double* out);
+
+/* Schwarz factors of Eq. 7 for every shell pair: Q[i*nshell+j] (HOST, symmetric). */
+eri_status eri_schwarz(const eri_plan* plan, double* Q);
+
+/*
+ * Rys roots and weights on the device, for testing the quadrature of Eq. 1:
+ * for each T[t] (t < n, T >= 0) writes u[t*N+r] = t_r^2 (ascending) and
+ * w[t*N+r], with sum_r w = F_0(T).  1 <= N <= 9.  Host arrays.  Synchronous.
+ */
+eri_status eri_rys_roots(int N, int n, const double* T, double* u, double* w);
+
+/* Counters of the last eri_jk call (synchronises that call's stream). */
+eri_status eri_flop_stats(eri_plan* plan, eri_stats* out);
+
+/* Measured FP64 and FP32 FMA-pipe throughput of device 0 (TFLOP/s), by a timed
+ * register-resident FMA loop; the denominators of the fraction-of-peak figures. */
+eri_status eri_probe_fma_peak(double* fp64_tflops, double* fp32_tflops);
+
+/* Message of the last failure on this thread ("" if none). */
+const char* eri_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ERI_H */
