@@ -1,0 +1,100 @@
+// Internal data layout shared by the host planner and the CUDA kernels.
+// Plain structs only (no CUDA types) so both g++ and nvcc can include it.
+#pragma once
+#include <stdint.h>
+
+#define ERI_LMAX 4
+#define ERI_NPAIRTYPE 15          // canonical pair types (l0 >= l1), l <= 4
+#define ERI_MAXCART 165           // Cartesian triples with l <= 8
+
+// One primitive pair (Gaussian product of Eq. 2's primitives on the pair's two
+// centres A, B).  64 bytes, 16-byte aligned, so a pair loads as four double2.
+struct PrimPair {
+  double zeta;     // alpha + beta
+  double P[3];     // (alpha A + beta B) / zeta
+  double PA[3];    // P - A
+  double E;        // sqrt(2) pi^(5/4) / zeta * exp(-alpha beta |A-B|^2 / zeta) * c_alpha c_beta
+};
+
+// One shell pair in canonical orientation (l of sh0 >= l of sh1).  64 bytes.
+struct ShellPair {
+  int sh0, sh1;    // shell indices
+  int bf0, bf1;    // first basis function of each shell
+  int prim_off;    // first PrimPair
+  int nprim;       // K_sh0 * K_sh1
+  int ptype;       // l0 * (l0 + 1) / 2 + l1
+  int pair_id;     // index among all pairs i >= j (identifies the unordered pair)
+  double AB[3];    // A - B (A = centre of sh0)
+  double Q;        // Cauchy-Schwarz factor of Eq. 7
+};
+
+// Static description of one angular-momentum class (la lb | lc ld).
+struct ClassDesc {
+  int la, lb, lc, ld;
+  int nroots;            // floor((la+lb+lc+ld)/2) + 1
+  int Le, Lf;            // la + lb, lc + ld
+  int nI;                // (Le+1)(Lf+1) 2D-integral entries per axis and root
+  int ne, nf;            // Cartesian e with la <= |e| <= Le, f with lc <= |f| <= Lf
+  int nout;              // ne * nf contracted [e0|f0] values
+  int na, nb, nc, nd;    // shell sizes
+  int e_base, f_base;    // global Cartesian index of the first e / f
+  int npass;             // output chunks of TS*G values
+  int bp;                // primitive quartets per batch (team kernels)
+  int team_doubles;      // shared-memory doubles per team
+  int hrr_doubles;       // size of one HRR ping-pong buffer (doubles)
+  long long scratch_per_team;  // global scratch doubles per team
+  const uint32_t* outidx;      // [nout] packed 2D offsets ix | iy << 8 | iz << 16
+};
+
+enum { KMODE_JK = 0, KMODE_BLOCK = 1, KMODE_SCHWARZ = 2 };
+
+struct KernelArgs {
+  ClassDesc c;
+  const ShellPair* pairs;
+  const PrimPair* prims;
+  // task space: bra pairs [bra0, bra0+nbra), ket pairs [ket0, ket0+nket); tri = same range, ket <= bra
+  int bra0, nbra, ket0, nket, tri;
+  long long ntask;
+  // screening (KMODE_JK)
+  const double* Dmax;    // [nsh][nsh]
+  int nsh;
+  double tau;
+  // densities and outputs (KMODE_JK): row-major [nD][nbf][nbf]
+  const double* D;
+  double* J;
+  double* K;
+  int nD, nbf, want;
+  // KMODE_BLOCK / KMODE_SCHWARZ: explicit tasks (bra, ket) and outputs
+  int mode;
+  const int* tasklist;   // [2*ntask]
+  double* blockout;      // KMODE_BLOCK: per task nabcd values, [cd][ab] layout as stored
+  const long long* blockoff;
+  double* qout;          // KMODE_SCHWARZ: per task max_{a,b} |(ab|ab)|
+  // scheduling, scratch, counters
+  unsigned long long* counter;
+  double* scratch;
+  unsigned long long* stats;   // [0] quartets computed, [1] primitive quartets
+  // Rys table for this class's root count
+  const double* rys_coef;      // block of this N
+  const double* rys_au;
+  const double* rys_aw;
+  int rys_tcut;
+};
+
+// Host-side launchers implemented in eri_kernels.cu.  All return a cudaError_t as int.
+#ifdef __cplusplus
+extern "C" {
+#endif
+int erik_upload_cart_tables(void);
+int erik_team_config(int ts, int* threads_per_block, int* max_g);
+int erik_blocks_per_sm(int ts, int smem_bytes, int* out);
+int erik_launch_class(int ts, const struct KernelArgs* a, int grid, int smem_bytes, void* stream);
+int erik_launch_dmax(const double* D, int nD, int nbf, int nsh, const int* sh_bf0, const int* sh_n,
+                     double* Dmax, void* stream);
+int erik_launch_symmetrize(double* M, int nD, int nbf, void* stream);
+int erik_launch_rys(int N, int n, const double* T, double* u, double* w, const double* coef,
+                    const double* au, const double* aw, int tcut, void* stream);
+int erik_probe_fma(double* fp64_tflops, double* fp32_tflops);
+#ifdef __cplusplus
+}
+#endif

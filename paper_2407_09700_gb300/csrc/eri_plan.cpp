@@ -1,0 +1,778 @@
+// Host planner and C-ABI of liberi (see include/eri.h).
+//
+// Plan creation follows Alg. 1 of Sec. 3: shells are paired (i >= j), each pair
+// gets its primitive-pair data (Gaussian product theorem applied to the
+// primitives of Eq. 2), Cauchy-Schwarz factors Q_ij (Eq. 7) are computed on the
+// GPU from the diagonal quartets (ij|ij), pairs with Q <= tau are dropped and
+// the rest are grouped by angular-momentum type (l0 >= l1) and sorted by
+// contraction depth.  eri_jk then forms the density block maxima (Eq. 9),
+// launches one class kernel per pair of pair types and symmetrises J and K.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/eri.h"
+#include "eri_internal.h"
+#include "rys_table.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+eri_status fail(eri_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+#define CUDA_TRY(expr)                                                                      \
+  do {                                                                                      \
+    cudaError_t _e = (cudaError_t)(expr);                                                   \
+    if (_e != cudaSuccess) {                                                                \
+      if (_e == cudaErrorMemoryAllocation)                                                  \
+        return fail(ERI_ERR_OOM, "%s: %s", #expr, cudaGetErrorString(_e));                  \
+      return fail(ERI_ERR_CUDA, "%s: %s (%s:%d)", #expr, cudaGetErrorString(_e), __FILE__, \
+                  __LINE__);                                                                \
+    }                                                                                       \
+  } while (0)
+
+inline int ncart(int l) { return (l + 1) * (l + 2) / 2; }
+inline int cart_below(int l) { return l * (l + 1) * (l + 2) / 6; }
+inline int ptype_of(int l0, int l1) { return l0 * (l0 + 1) / 2 + l1; }
+inline void ptype_ls(int t, int* l0, int* l1) {
+  int a = 0;
+  while ((a + 1) * (a + 2) / 2 <= t) ++a;
+  *l0 = a;
+  *l1 = t - a * (a + 1) / 2;
+}
+
+// Cartesian triples in x-descending order, l = 0..8 (host copy of the device table).
+struct CartTab {
+  int lx[ERI_MAXCART], ly[ERI_MAXCART], lz[ERI_MAXCART];
+  CartTab() {
+    int g = 0;
+    for (int l = 0; l <= 8; ++l)
+      for (int x = l; x >= 0; --x)
+        for (int y = l - x; y >= 0; --y) {
+          lx[g] = x;
+          ly[g] = y;
+          lz[g] = l - x - y;
+          ++g;
+        }
+  }
+};
+const CartTab& cart() {
+  static CartTab t;
+  return t;
+}
+
+// ---------------------------------------------------------------- per-device shared state
+struct DeviceState {
+  bool ready = false;
+  double* rys_coef = nullptr;
+  double* rys_au = nullptr;
+  double* rys_aw = nullptr;
+  uint32_t* outidx = nullptr;        // all 225 class index tables
+  ClassDesc classes[ERI_NPAIRTYPE][ERI_NPAIRTYPE];
+  int ts[ERI_NPAIRTYPE][ERI_NPAIRTYPE];
+  int sms = 0;
+};
+std::mutex g_dev_mu;
+DeviceState g_dev[64];
+
+int choose_ts(int nout) {
+  if (nout <= 32) return 1;
+  if (nout <= 8 * 32) return 8;
+  return 32;
+}
+
+// Fill the static part of a class descriptor (no device pointers).
+void make_class(int la, int lb, int lc, int ld, ClassDesc* c, int* ts, std::vector<uint32_t>* idx) {
+  c->la = la; c->lb = lb; c->lc = lc; c->ld = ld;
+  c->nroots = (la + lb + lc + ld) / 2 + 1;
+  c->Le = la + lb;
+  c->Lf = lc + ld;
+  c->nI = (c->Le + 1) * (c->Lf + 1);
+  c->e_base = cart_below(la);
+  c->f_base = cart_below(lc);
+  c->ne = cart_below(c->Le + 1) - c->e_base;
+  c->nf = cart_below(c->Lf + 1) - c->f_base;
+  c->nout = c->ne * c->nf;
+  c->na = ncart(la); c->nb = ncart(lb); c->nc = ncart(lc); c->nd = ncart(ld);
+  const CartTab& ct = cart();
+  idx->clear();
+  const int L1 = c->Lf + 1;
+  for (int ie = 0; ie < c->ne; ++ie)
+    for (int jf = 0; jf < c->nf; ++jf) {
+      const int e = c->e_base + ie, f = c->f_base + jf;
+      const uint32_t ix = ct.lx[e] * L1 + ct.lx[f];
+      const uint32_t iy = ct.ly[e] * L1 + ct.ly[f];
+      const uint32_t iz = ct.lz[e] * L1 + ct.lz[f];
+      idx->push_back(ix | (iy << 8) | (iz << 16));
+    }
+  *ts = choose_ts(c->nout);
+  c->npass = (c->nout + *ts * 32 - 1) / (*ts * 32);
+  const int per_prim = 24 + 3 * c->nroots * c->nI;
+  if (*ts == 1) {
+    c->bp = 1;
+  } else {
+    const int budget = (*ts == 8) ? 768 : 3072;
+    c->bp = std::max(1, std::min(32, budget / per_prim));
+  }
+  c->team_doubles = c->bp * per_prim;
+  // HRR ping-pong size: max level size of the bra (vector nf) and ket (vector nab) passes
+  long long m = 1;
+  for (int k = 1; k <= lb; ++k) {
+    long long na = cart_below(la + lb - k + 1) - cart_below(la);
+    m = std::max(m, na * ncart(k) * c->nf);
+  }
+  for (int k = 1; k <= ld; ++k) {
+    long long nc = cart_below(lc + ld - k + 1) - cart_below(lc);
+    m = std::max(m, nc * ncart(k) * (long long)(c->na * c->nb));
+  }
+  c->hrr_doubles = (int)((m + 1) & ~1LL);
+  c->scratch_per_team = ((long long)c->nout + 1) / 2 * 2 + 2LL * c->hrr_doubles;
+  c->outidx = nullptr;
+}
+
+eri_status device_init(int dev, DeviceState** out) {
+  std::lock_guard<std::mutex> lk(g_dev_mu);
+  if (dev < 0 || dev >= 64) return fail(ERI_ERR_ARG, "device index %d out of range", dev);
+  DeviceState& s = g_dev[dev];
+  if (!s.ready) {
+    CUDA_TRY(erik_upload_cart_tables());
+    size_t ncoef = (size_t)RYS_NCOEF, nas = (size_t)RYS_ASYM_OFFSET[RYS_NMAX] + RYS_NMAX;
+    CUDA_TRY(cudaMalloc(&s.rys_coef, sizeof(double) * ncoef));
+    CUDA_TRY(cudaMalloc(&s.rys_au, sizeof(double) * nas));
+    CUDA_TRY(cudaMalloc(&s.rys_aw, sizeof(double) * nas));
+    CUDA_TRY(cudaMemcpy(s.rys_coef, RYS_COEF, sizeof(double) * ncoef, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(s.rys_au, RYS_ASYM_U, sizeof(double) * nas, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(s.rys_aw, RYS_ASYM_W, sizeof(double) * nas, cudaMemcpyHostToDevice));
+    std::vector<uint32_t> all, one;
+    size_t offs[ERI_NPAIRTYPE][ERI_NPAIRTYPE];
+    for (int X = 0; X < ERI_NPAIRTYPE; ++X)
+      for (int Y = 0; Y < ERI_NPAIRTYPE; ++Y) {
+        int la, lb, lc, ld;
+        ptype_ls(X, &la, &lb);
+        ptype_ls(Y, &lc, &ld);
+        make_class(la, lb, lc, ld, &s.classes[X][Y], &s.ts[X][Y], &one);
+        offs[X][Y] = all.size();
+        all.insert(all.end(), one.begin(), one.end());
+      }
+    CUDA_TRY(cudaMalloc(&s.outidx, sizeof(uint32_t) * all.size()));
+    CUDA_TRY(cudaMemcpy(s.outidx, all.data(), sizeof(uint32_t) * all.size(), cudaMemcpyHostToDevice));
+    for (int X = 0; X < ERI_NPAIRTYPE; ++X)
+      for (int Y = 0; Y < ERI_NPAIRTYPE; ++Y) s.classes[X][Y].outidx = s.outidx + offs[X][Y];
+    CUDA_TRY(cudaDeviceGetAttribute(&s.sms, cudaDevAttrMultiProcessorCount, dev));
+    s.ready = true;
+  }
+  *out = &s;
+  return ERI_OK;
+}
+
+// FP64 operation count of the class kernel's algorithm (an FMA counts as 2).
+void class_model_flops(const ClassDesc& c, int nD, int want, double* per_prim, double* per_quartet) {
+  const int N = c.nroots, Le = c.Le, Lf = c.Lf;
+  double vrr = 0.0;                                   // one rys_2d call
+  if (Le >= 1) vrr += 1;
+  vrr += 4.0 * std::max(0, Le - 1);                   // fma + mul + running add
+  if (Lf >= 1) vrr += 1 + 4.0 * Le;
+  if (Lf >= 2) vrr += (Lf - 1) * (3.0 + 6.0 * Le + 1);
+  const double setup = 40.0;                          // Gaussian products, rsqrt, T, table lookup
+  const double root = 2 * 24.0 + 14.0;                // two degree-11 Horner sums + coefficients
+  *per_prim = setup + N * (root + 3 * vrr) + 3.0 * N * c.nout;
+  double hrr = 0.0;
+  for (int k = 1; k <= c.lb; ++k)
+    hrr += 2.0 * (cart_below(c.la + c.lb - k + 1) - cart_below(c.la)) * ncart(k) * c.nf;
+  for (int k = 1; k <= c.ld; ++k)
+    hrr += 2.0 * (cart_below(c.lc + c.ld - k + 1) - cart_below(c.lc)) * ncart(k) * c.na * c.nb;
+  const double nabcd = (double)c.na * c.nb * c.nc * c.nd;
+  const double dig = 2.0 * nabcd * nD * (((want & 1) ? 2 : 0) + ((want & 2) ? 4 : 0));
+  *per_quartet = hrr + dig;
+}
+
+void normalise(int nshell, const int* l, const int* nprim, const int* off, const double* exps,
+               const double* raw, std::vector<double>& out) {
+  for (int s = 0; s < nshell; ++s) {
+    const int L = l[s], K = nprim[s], o = off[s];
+    double df = 1.0;
+    for (int k = 2 * L - 1; k > 1; k -= 2) df *= k;
+    for (int p = 0; p < K; ++p) {
+      const double a = exps[o + p];
+      out[o + p] = raw[o + p] * std::pow(2.0 * a / M_PI, 0.75) * std::pow(4.0 * a, 0.5 * L) / std::sqrt(df);
+    }
+    double S = 0.0;
+    for (int p = 0; p < K; ++p)
+      for (int q = 0; q < K; ++q) {
+        const double s2 = exps[o + p] + exps[o + q];
+        S += out[o + p] * out[o + q] * df / std::pow(2.0 * s2, L) * std::pow(M_PI / s2, 1.5);
+      }
+    const double f = 1.0 / std::sqrt(S);
+    for (int p = 0; p < K; ++p) out[o + p] *= f;
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- the plan
+struct eri_plan {
+  int device = 0;
+  DeviceState* dev = nullptr;
+  eri_opts opts{};
+  int natm = 0, nshell = 0, nbf = 0;
+  std::vector<double> coords;
+  std::vector<int> sh_l, sh_atom, sh_nprim, sh_off, sh_bf0;
+  std::vector<double> exps, coefs;
+  // all pairs (i >= j) in canonical orientation, grouped by type then depth
+  std::vector<ShellPair> pairs_all;
+  std::vector<int> pair_index;       // [i*nshell + j] -> index into pairs_all (both orders)
+  std::vector<PrimPair> prims;
+  int type_off_all[ERI_NPAIRTYPE] = {0}, type_cnt_all[ERI_NPAIRTYPE] = {0};
+  // kept pairs (Q > tau)
+  int type_off[ERI_NPAIRTYPE] = {0}, type_cnt[ERI_NPAIRTYPE] = {0};
+  int npairs_kept = 0;
+  std::vector<double> Q;             // [nshell*nshell]
+  // device buffers
+  ShellPair* d_pairs_all = nullptr;
+  ShellPair* d_pairs = nullptr;
+  PrimPair* d_prims = nullptr;
+  int* d_sh_bf0 = nullptr;
+  int* d_sh_n = nullptr;
+  double* d_Dmax = nullptr;
+  unsigned long long* d_counters = nullptr;   // one per class launch
+  unsigned long long* d_stats = nullptr;      // [225][2]
+  double* d_scratch = nullptr;
+  size_t scratch_doubles = 0;
+  int* d_tasks = nullptr;
+  size_t tasks_cap = 0;
+  double* d_out = nullptr;
+  size_t out_cap = 0;
+  long long* d_off = nullptr;
+  size_t off_cap = 0;
+  double* d_host_io = nullptr;                // D, J, K staging for eri_jk_host
+  size_t host_io_cap = 0;
+  cudaStream_t last_stream = nullptr;
+  // last eri_jk bookkeeping
+  long long last_candidates = 0;
+  int last_nclasses = 0, last_nD = 1, last_want = 3;
+};
+
+namespace {
+
+eri_status ensure_scratch(eri_plan* p, size_t doubles) {
+  if (doubles <= p->scratch_doubles) return ERI_OK;
+  if (p->d_scratch) {
+    CUDA_TRY(cudaDeviceSynchronize());
+    cudaFree(p->d_scratch);
+    p->d_scratch = nullptr;
+    p->scratch_doubles = 0;
+  }
+  CUDA_TRY(cudaMalloc(&p->d_scratch, sizeof(double) * doubles));
+  p->scratch_doubles = doubles;
+  return ERI_OK;
+}
+
+template <typename T>
+eri_status ensure_buf(T** ptr, size_t* cap, size_t n) {
+  if (n <= *cap) return ERI_OK;
+  if (*ptr) {
+    CUDA_TRY(cudaDeviceSynchronize());
+    cudaFree(*ptr);
+    *ptr = nullptr;
+    *cap = 0;
+  }
+  CUDA_TRY(cudaMalloc(ptr, sizeof(T) * n));
+  *cap = n;
+  return ERI_OK;
+}
+
+// Grid and dynamic shared memory for one class launch.
+eri_status launch_shape(eri_plan* p, int X, int Y, long long nteams_needed, int* grid, int* smem,
+                        int* ts_out) {
+  const ClassDesc& c = p->dev->classes[X][Y];
+  const int ts = p->dev->ts[X][Y];
+  const int teams_per_block = 128 / ts;
+  *smem = (int)(sizeof(double) * (size_t)c.team_doubles * teams_per_block);
+  if (*smem > 200 * 1024) return fail(ERI_ERR_ARG, "class (%d%d|%d%d) needs %d bytes of shared memory", c.la, c.lb, c.lc, c.ld, *smem);
+  int bps = 0;
+  CUDA_TRY(erik_blocks_per_sm(ts, *smem, &bps));
+  if (bps < 1) bps = 1;
+  long long full = (long long)p->dev->sms * bps;
+  long long need = (nteams_needed + teams_per_block - 1) / teams_per_block;
+  *grid = (int)std::max(1LL, std::min(full, need));
+  *ts_out = ts;
+  return ERI_OK;
+}
+
+KernelArgs base_args(eri_plan* p, int X, int Y) {
+  KernelArgs a;
+  memset(&a, 0, sizeof(a));
+  a.c = p->dev->classes[X][Y];
+  a.prims = p->d_prims;
+  a.nsh = p->nshell;
+  a.nbf = p->nbf;
+  const int N = a.c.nroots;
+  a.rys_coef = p->dev->rys_coef + RYS_COEF_OFFSET[N];
+  a.rys_au = p->dev->rys_au + RYS_ASYM_OFFSET[N];
+  a.rys_aw = p->dev->rys_aw + RYS_ASYM_OFFSET[N];
+  a.rys_tcut = RYS_TCUT[N];
+  return a;
+}
+
+// Run explicit (bra, ket) tasks of one class in KMODE_BLOCK or KMODE_SCHWARZ on the all-pairs array.
+eri_status run_explicit(eri_plan* p, int X, int Y, int mode, const std::vector<int>& tasks,
+                        const std::vector<long long>& offs, size_t out_doubles, cudaStream_t st) {
+  const long long nt = (long long)tasks.size() / 2;
+  if (nt == 0) return ERI_OK;
+  eri_status s;
+  if ((s = ensure_buf(&p->d_tasks, &p->tasks_cap, tasks.size())) != ERI_OK) return s;
+  if ((s = ensure_buf(&p->d_out, &p->out_cap, std::max<size_t>(out_doubles, 1))) != ERI_OK) return s;
+  if (mode == KMODE_BLOCK && (s = ensure_buf(&p->d_off, &p->off_cap, offs.size())) != ERI_OK) return s;
+  int grid, smem, ts;
+  if ((s = launch_shape(p, X, Y, nt, &grid, &smem, &ts)) != ERI_OK) return s;
+  const ClassDesc& c = p->dev->classes[X][Y];
+  size_t need = (size_t)grid * (size_t)(128 / ts) * (size_t)c.scratch_per_team;
+  if ((s = ensure_scratch(p, need)) != ERI_OK) return s;
+  CUDA_TRY(cudaMemcpyAsync(p->d_tasks, tasks.data(), sizeof(int) * tasks.size(), cudaMemcpyHostToDevice, st));
+  if (mode == KMODE_BLOCK)
+    CUDA_TRY(cudaMemcpyAsync(p->d_off, offs.data(), sizeof(long long) * offs.size(), cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemsetAsync(p->d_counters, 0, sizeof(unsigned long long), st));
+  KernelArgs a = base_args(p, X, Y);
+  a.pairs = p->d_pairs_all;
+  a.ntask = nt;
+  a.mode = mode;
+  a.tasklist = p->d_tasks;
+  a.blockout = p->d_out;
+  a.blockoff = p->d_off;
+  a.qout = p->d_out;
+  a.counter = p->d_counters;
+  a.scratch = p->d_scratch;
+  a.stats = nullptr;
+  CUDA_TRY(erik_launch_class(ts, &a, grid, smem, st));
+  return ERI_OK;
+}
+
+eri_status validate_basis(const eri_basis* b) {
+  if (!b) return fail(ERI_ERR_ARG, "basis is NULL");
+  if (b->natm < 1 || !b->coords) return fail(ERI_ERR_ARG, "natm must be >= 1 with coords");
+  if (b->nshell < 1 || !b->shell_atom || !b->shell_l || !b->shell_nprim || !b->shell_off || !b->exps ||
+      !b->coefs)
+    return fail(ERI_ERR_ARG, "nshell must be >= 1 and every shell array non-NULL");
+  for (int i = 0; i < 3 * b->natm; ++i)
+    if (!std::isfinite(b->coords[i])) return fail(ERI_ERR_BASIS, "coordinate %d is not finite", i);
+  for (int s = 0; s < b->nshell; ++s) {
+    if (b->shell_l[s] < 0) return fail(ERI_ERR_BASIS, "shell %d has l < 0", s);
+    if (b->shell_l[s] > ERI_LMAX) return fail(ERI_ERR_UNSUPPORTED_L, "shell %d has l = %d > 4", s, b->shell_l[s]);
+    if (b->shell_nprim[s] < 1) return fail(ERI_ERR_BASIS, "shell %d has nprim < 1", s);
+    if (b->shell_off[s] < 0) return fail(ERI_ERR_BASIS, "shell %d has a negative offset", s);
+    if (b->shell_atom[s] < 0 || b->shell_atom[s] >= b->natm) return fail(ERI_ERR_BASIS, "shell %d has a bad atom index", s);
+    for (int p = 0; p < b->shell_nprim[s]; ++p) {
+      const double e = b->exps[b->shell_off[s] + p], c = b->coefs[b->shell_off[s] + p];
+      if (!std::isfinite(e) || !(e > 0)) return fail(ERI_ERR_BASIS, "shell %d primitive %d: exponent must be finite and > 0", s, p);
+      if (!std::isfinite(c)) return fail(ERI_ERR_BASIS, "shell %d primitive %d: coefficient is not finite", s, p);
+    }
+  }
+  return ERI_OK;
+}
+
+}  // namespace
+
+// ================================================================= C-ABI
+extern "C" {
+
+const char* eri_last_error(void) { return g_err.c_str(); }
+
+int eri_plan_nbf(const eri_plan* p) { return p ? p->nbf : -1; }
+
+eri_status eri_plan_destroy(eri_plan* p) {
+  if (!p) return ERI_OK;
+  cudaSetDevice(p->device);
+  cudaDeviceSynchronize();
+  void* bufs[] = {p->d_pairs_all, p->d_pairs, p->d_prims, p->d_sh_bf0, p->d_sh_n, p->d_Dmax, p->d_counters,
+                  p->d_stats, p->d_scratch, p->d_tasks, p->d_out, p->d_off, p->d_host_io};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  delete p;
+  return ERI_OK;
+}
+
+eri_status eri_plan_create(const eri_basis* basis, const eri_opts* opts, void* cuda_stream, eri_plan** out) {
+  g_err.clear();
+  if (!out) return fail(ERI_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!opts) return fail(ERI_ERR_ARG, "opts is NULL");
+  if (!(opts->screen_thresh >= 0) || !std::isfinite(opts->screen_thresh))
+    return fail(ERI_ERR_ARG, "screen_thresh must be finite and >= 0");
+  if (opts->max_nd < 1) return fail(ERI_ERR_ARG, "max_nd must be >= 1");
+  if (opts->precision != ERI_FP64 && opts->precision != ERI_MIXED) return fail(ERI_ERR_ARG, "unknown precision mode");
+  eri_status s = validate_basis(basis);
+  if (s != ERI_OK) return s;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+    cudaGetLastError();
+    return fail(ERI_ERR_NO_DEVICE, "no CUDA device is visible");
+  }
+  eri_plan* p = new (std::nothrow) eri_plan();
+  if (!p) return fail(ERI_ERR_OOM, "host allocation failed");
+  cudaGetDevice(&p->device);
+  if ((s = device_init(p->device, &p->dev)) != ERI_OK) { delete p; return s; }
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  p->opts = *opts;
+  p->natm = basis->natm;
+  p->nshell = basis->nshell;
+  p->coords.assign(basis->coords, basis->coords + 3 * basis->natm);
+  p->sh_l.assign(basis->shell_l, basis->shell_l + p->nshell);
+  p->sh_atom.assign(basis->shell_atom, basis->shell_atom + p->nshell);
+  p->sh_nprim.assign(basis->shell_nprim, basis->shell_nprim + p->nshell);
+  p->sh_off.assign(basis->shell_off, basis->shell_off + p->nshell);
+  int nprim_total = 0;
+  for (int i = 0; i < p->nshell; ++i) nprim_total = std::max(nprim_total, p->sh_off[i] + p->sh_nprim[i]);
+  p->exps.assign(basis->exps, basis->exps + nprim_total);
+  p->coefs.assign(basis->coefs, basis->coefs + nprim_total);
+  if (basis->normalise) normalise(p->nshell, p->sh_l.data(), p->sh_nprim.data(), p->sh_off.data(), p->exps.data(), basis->coefs, p->coefs);
+  p->sh_bf0.resize(p->nshell);
+  std::vector<int> sh_n(p->nshell);
+  for (int i = 0; i < p->nshell; ++i) {
+    p->sh_bf0[i] = p->nbf;
+    sh_n[i] = ncart(p->sh_l[i]);
+    p->nbf += sh_n[i];
+  }
+
+  // ---- shell pairs (i >= j) in canonical orientation, grouped by type and depth
+  struct Tmp { int t, np, i, j; };
+  std::vector<Tmp> tmp;
+  for (int i = 0; i < p->nshell; ++i)
+    for (int j = 0; j <= i; ++j) {
+      int a = i, b = j;
+      if (p->sh_l[b] > p->sh_l[a]) std::swap(a, b);
+      tmp.push_back({ptype_of(p->sh_l[a], p->sh_l[b]), p->sh_nprim[a] * p->sh_nprim[b], a, b});
+    }
+  std::stable_sort(tmp.begin(), tmp.end(), [](const Tmp& x, const Tmp& y) {
+    return x.t != y.t ? x.t < y.t : x.np > y.np;
+  });
+  const double pref = std::sqrt(2.0) * std::pow(M_PI, 1.25);
+  p->pair_index.assign((size_t)p->nshell * p->nshell, -1);
+  for (size_t k = 0; k < tmp.size(); ++k) {
+    const Tmp& t = tmp[k];
+    ShellPair sp;
+    memset(&sp, 0, sizeof(sp));
+    sp.sh0 = t.i;
+    sp.sh1 = t.j;
+    sp.bf0 = p->sh_bf0[t.i];
+    sp.bf1 = p->sh_bf0[t.j];
+    sp.prim_off = (int)p->prims.size();
+    sp.nprim = t.np;
+    sp.ptype = t.t;
+    sp.pair_id = (int)k;
+    const double* A = &p->coords[3 * p->sh_atom[t.i]];
+    const double* B = &p->coords[3 * p->sh_atom[t.j]];
+    double AB2 = 0.0;
+    for (int x = 0; x < 3; ++x) {
+      sp.AB[x] = A[x] - B[x];
+      AB2 += sp.AB[x] * sp.AB[x];
+    }
+    for (int u = 0; u < p->sh_nprim[t.i]; ++u)
+      for (int v = 0; v < p->sh_nprim[t.j]; ++v) {
+        const double al = p->exps[p->sh_off[t.i] + u], be = p->exps[p->sh_off[t.j] + v];
+        const double ca = p->coefs[p->sh_off[t.i] + u], cb = p->coefs[p->sh_off[t.j] + v];
+        PrimPair pp;
+        pp.zeta = al + be;
+        for (int x = 0; x < 3; ++x) {
+          pp.P[x] = (al * A[x] + be * B[x]) / pp.zeta;
+          pp.PA[x] = pp.P[x] - A[x];
+        }
+        pp.E = pref / pp.zeta * std::exp(-al * be / pp.zeta * AB2) * ca * cb;
+        p->prims.push_back(pp);
+      }
+    p->pairs_all.push_back(sp);
+    p->pair_index[(size_t)t.i * p->nshell + t.j] = (int)k;
+    p->pair_index[(size_t)t.j * p->nshell + t.i] = (int)k;
+    p->type_cnt_all[t.t]++;
+  }
+  for (int t = 1; t < ERI_NPAIRTYPE; ++t) p->type_off_all[t] = p->type_off_all[t - 1] + p->type_cnt_all[t - 1];
+
+  auto cleanup = [&](eri_status e) { eri_plan_destroy(p); return e; };
+  const size_t npair = p->pairs_all.size();
+  if (cudaMalloc(&p->d_pairs_all, sizeof(ShellPair) * npair) != cudaSuccess ||
+      cudaMalloc(&p->d_pairs, sizeof(ShellPair) * npair) != cudaSuccess ||
+      cudaMalloc(&p->d_prims, sizeof(PrimPair) * p->prims.size()) != cudaSuccess ||
+      cudaMalloc(&p->d_sh_bf0, sizeof(int) * p->nshell) != cudaSuccess ||
+      cudaMalloc(&p->d_sh_n, sizeof(int) * p->nshell) != cudaSuccess ||
+      cudaMalloc(&p->d_Dmax, sizeof(double) * p->nshell * p->nshell) != cudaSuccess ||
+      cudaMalloc(&p->d_counters, sizeof(unsigned long long) * 256) != cudaSuccess ||
+      cudaMalloc(&p->d_stats, sizeof(unsigned long long) * 2 * 256) != cudaSuccess) {
+    cudaGetLastError();
+    return cleanup(fail(ERI_ERR_OOM, "device allocation failed in eri_plan_create"));
+  }
+#define PLAN_TRY(expr)                                        \
+  do {                                                        \
+    cudaError_t _e = (cudaError_t)(expr);                     \
+    if (_e != cudaSuccess)                                    \
+      return cleanup(fail(ERI_ERR_CUDA, "%s: %s", #expr, cudaGetErrorString(_e))); \
+  } while (0)
+  PLAN_TRY(cudaMemcpyAsync(p->d_pairs_all, p->pairs_all.data(), sizeof(ShellPair) * npair, cudaMemcpyHostToDevice, st));
+  PLAN_TRY(cudaMemcpyAsync(p->d_prims, p->prims.data(), sizeof(PrimPair) * p->prims.size(), cudaMemcpyHostToDevice, st));
+  PLAN_TRY(cudaMemcpyAsync(p->d_sh_bf0, p->sh_bf0.data(), sizeof(int) * p->nshell, cudaMemcpyHostToDevice, st));
+  PLAN_TRY(cudaMemcpyAsync(p->d_sh_n, sh_n.data(), sizeof(int) * p->nshell, cudaMemcpyHostToDevice, st));
+  PLAN_TRY(cudaMemsetAsync(p->d_stats, 0, sizeof(unsigned long long) * 2 * 256, st));
+
+  // ---- Schwarz factors (Eq. 7) from the diagonal quartets (ij|ij), one class (X|X) at a time
+  p->Q.assign((size_t)p->nshell * p->nshell, 0.0);
+  std::vector<double> qmax(npair, 0.0);
+  for (int X = 0; X < ERI_NPAIRTYPE; ++X) {
+    const int n = p->type_cnt_all[X];
+    if (n == 0) continue;
+    std::vector<int> tasks(2 * n);
+    for (int k = 0; k < n; ++k) tasks[2 * k] = tasks[2 * k + 1] = p->type_off_all[X] + k;
+    if ((s = run_explicit(p, X, X, KMODE_SCHWARZ, tasks, {}, n, st)) != ERI_OK) return cleanup(s);
+    PLAN_TRY(cudaMemcpyAsync(qmax.data() + p->type_off_all[X], p->d_out, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+    PLAN_TRY(cudaStreamSynchronize(st));
+  }
+  for (size_t k = 0; k < npair; ++k) {
+    ShellPair& sp = p->pairs_all[k];
+    sp.Q = std::sqrt(qmax[k]);
+    p->Q[(size_t)sp.sh0 * p->nshell + sp.sh1] = sp.Q;
+    p->Q[(size_t)sp.sh1 * p->nshell + sp.sh0] = sp.Q;
+  }
+  PLAN_TRY(cudaMemcpyAsync(p->d_pairs_all, p->pairs_all.data(), sizeof(ShellPair) * npair, cudaMemcpyHostToDevice, st));
+
+  // ---- kept pairs: Q > tau, still grouped by type and sorted by depth
+  std::vector<ShellPair> kept;
+  for (int X = 0; X < ERI_NPAIRTYPE; ++X) {
+    p->type_off[X] = (int)kept.size();
+    for (int k = 0; k < p->type_cnt_all[X]; ++k) {
+      const ShellPair& sp = p->pairs_all[p->type_off_all[X] + k];
+      if (sp.Q > p->opts.screen_thresh) kept.push_back(sp);
+    }
+    p->type_cnt[X] = (int)kept.size() - p->type_off[X];
+  }
+  p->npairs_kept = (int)kept.size();
+  if (!kept.empty())
+    PLAN_TRY(cudaMemcpyAsync(p->d_pairs, kept.data(), sizeof(ShellPair) * kept.size(), cudaMemcpyHostToDevice, st));
+  PLAN_TRY(cudaStreamSynchronize(st));
+#undef PLAN_TRY
+  *out = p;
+  return ERI_OK;
+}
+
+eri_status eri_jk(eri_plan* p, const double* D, int nD, double* J, double* K, int flags, void* cuda_stream) {
+  g_err.clear();
+  if (!p) return fail(ERI_ERR_ARG, "plan is NULL");
+  if (!D) return fail(ERI_ERR_ARG, "D is NULL");
+  if (nD < 1 || nD > p->opts.max_nd) return fail(ERI_ERR_ARG, "nD = %d outside [1, %d]", nD, p->opts.max_nd);
+  const int want = flags & 3;
+  if (want == 0) return fail(ERI_ERR_ARG, "flags request neither J nor K");
+  if ((want & 1) && !J) return fail(ERI_ERR_ARG, "J requested but NULL");
+  if ((want & 2) && !K) return fail(ERI_ERR_ARG, "K requested but NULL");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const size_t mat = (size_t)nD * p->nbf * p->nbf;
+  if (want & 1) CUDA_TRY(cudaMemsetAsync(J, 0, sizeof(double) * mat, st));
+  if (want & 2) CUDA_TRY(cudaMemsetAsync(K, 0, sizeof(double) * mat, st));
+  CUDA_TRY(erik_launch_dmax(D, nD, p->nbf, p->nshell, p->d_sh_bf0, p->d_sh_n, p->d_Dmax, st));
+  CUDA_TRY(cudaMemsetAsync(p->d_counters, 0, sizeof(unsigned long long) * 256, st));
+  CUDA_TRY(cudaMemsetAsync(p->d_stats, 0, sizeof(unsigned long long) * 2 * 256, st));
+
+  // scratch for the largest class launch
+  struct L { int X, Y, grid, smem, ts; long long nt; };
+  std::vector<L> launches;
+  size_t need = 0;
+  long long cand = 0;
+  for (int X = 0; X < ERI_NPAIRTYPE; ++X) {
+    if (!p->type_cnt[X]) continue;
+    for (int Y = 0; Y <= X; ++Y) {
+      if (!p->type_cnt[Y]) continue;
+      const long long nx = p->type_cnt[X], ny = p->type_cnt[Y];
+      const long long nt = (X == Y) ? nx * (nx + 1) / 2 : nx * ny;
+      L l{X, Y, 0, 0, 0, nt};
+      eri_status s = launch_shape(p, X, Y, nt, &l.grid, &l.smem, &l.ts);
+      if (s != ERI_OK) return s;
+      need = std::max(need, (size_t)l.grid * (size_t)(128 / l.ts) * (size_t)p->dev->classes[X][Y].scratch_per_team);
+      launches.push_back(l);
+      cand += nt;
+    }
+  }
+  eri_status s = ensure_scratch(p, need);
+  if (s != ERI_OK) return s;
+  int li = 0;
+  for (const L& l : launches) {
+    KernelArgs a = base_args(p, l.X, l.Y);
+    a.pairs = p->d_pairs;
+    a.bra0 = p->type_off[l.X];
+    a.nbra = p->type_cnt[l.X];
+    a.ket0 = p->type_off[l.Y];
+    a.nket = p->type_cnt[l.Y];
+    a.tri = (l.X == l.Y);
+    a.ntask = l.nt;
+    a.Dmax = p->d_Dmax;
+    a.tau = p->opts.screen_thresh;
+    a.D = D;
+    a.J = J;
+    a.K = K;
+    a.nD = nD;
+    a.want = want;
+    a.mode = KMODE_JK;
+    a.counter = p->d_counters + li;
+    a.scratch = p->d_scratch;
+    a.stats = p->d_stats + 2 * (l.X * ERI_NPAIRTYPE + l.Y);
+    CUDA_TRY(erik_launch_class(l.ts, &a, l.grid, l.smem, st));
+    ++li;
+  }
+  if (want & 1) CUDA_TRY(erik_launch_symmetrize(J, nD, p->nbf, st));
+  if (want & 2) CUDA_TRY(erik_launch_symmetrize(K, nD, p->nbf, st));
+  p->last_stream = st;
+  p->last_candidates = cand;
+  p->last_nclasses = (int)launches.size();
+  p->last_nD = nD;
+  p->last_want = want;
+  return ERI_OK;
+}
+
+eri_status eri_jk_host(eri_plan* p, const double* D, int nD, double* J, double* K, int flags, void* cuda_stream) {
+  g_err.clear();
+  if (!p) return fail(ERI_ERR_ARG, "plan is NULL");
+  if (!D) return fail(ERI_ERR_ARG, "D is NULL");
+  if (nD < 1 || nD > p->opts.max_nd) return fail(ERI_ERR_ARG, "nD = %d outside [1, %d]", nD, p->opts.max_nd);
+  const int want = flags & 3;
+  if (want == 0) return fail(ERI_ERR_ARG, "flags request neither J nor K");
+  if ((want & 1) && !J) return fail(ERI_ERR_ARG, "J requested but NULL");
+  if ((want & 2) && !K) return fail(ERI_ERR_ARG, "K requested but NULL");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const size_t mat = (size_t)nD * p->nbf * p->nbf;
+  eri_status s = ensure_buf(&p->d_host_io, &p->host_io_cap, 3 * mat);
+  if (s != ERI_OK) return s;
+  double* dD = p->d_host_io;
+  double* dJ = dD + mat;
+  double* dK = dJ + mat;
+  CUDA_TRY(cudaMemcpyAsync(dD, D, sizeof(double) * mat, cudaMemcpyHostToDevice, st));
+  if ((s = eri_jk(p, dD, nD, dJ, dK, want, st)) != ERI_OK) return s;
+  if (want & 1) CUDA_TRY(cudaMemcpyAsync(J, dJ, sizeof(double) * mat, cudaMemcpyDeviceToHost, st));
+  if (want & 2) CUDA_TRY(cudaMemcpyAsync(K, dK, sizeof(double) * mat, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  return ERI_OK;
+}
+
+eri_status eri_shell_quartet(eri_plan* p, int i, int j, int k, int l, double* out) {
+  g_err.clear();
+  if (!p || !out) return fail(ERI_ERR_ARG, "plan or out is NULL");
+  const int ns = p->nshell;
+  if (i < 0 || j < 0 || k < 0 || l < 0 || i >= ns || j >= ns || k >= ns || l >= ns)
+    return fail(ERI_ERR_ARG, "shell index outside [0, %d)", ns);
+  const int pb = p->pair_index[(size_t)i * ns + j], pk = p->pair_index[(size_t)k * ns + l];
+  const ShellPair& B = p->pairs_all[pb];
+  const ShellPair& Kt = p->pairs_all[pk];
+  const int X = B.ptype, Y = Kt.ptype;
+  const ClassDesc& c = p->dev->classes[X][Y];
+  const size_t nblk = (size_t)c.na * c.nb * c.nc * c.nd;
+  std::vector<int> tasks = {pb, pk};
+  std::vector<long long> offs = {0};
+  cudaStream_t st = nullptr;
+  eri_status s = run_explicit(p, X, Y, KMODE_BLOCK, tasks, offs, nblk, st);
+  if (s != ERI_OK) return s;
+  std::vector<double> blk(nblk);
+  CUDA_TRY(cudaMemcpyAsync(blk.data(), p->d_out, sizeof(double) * nblk, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  // canonical block [a(sh0 of bra)][b(sh1)][c(sh0 of ket)][d(sh1)] -> requested (i j | k l)
+  const bool sw_b = (B.sh0 != i);
+  const bool sw_k = (Kt.sh0 != k);
+  const int ni = ncart(p->sh_l[i]), nj = ncart(p->sh_l[j]), nk = ncart(p->sh_l[k]), nl = ncart(p->sh_l[l]);
+  for (int x = 0; x < ni; ++x)
+    for (int y = 0; y < nj; ++y)
+      for (int z = 0; z < nk; ++z)
+        for (int w = 0; w < nl; ++w) {
+          const int a = sw_b ? y : x, b = sw_b ? x : y;
+          const int cc = sw_k ? w : z, d = sw_k ? z : w;
+          out[(((size_t)x * nj + y) * nk + z) * nl + w] = blk[(((size_t)a * c.nb + b) * c.nc + cc) * c.nd + d];
+        }
+  return ERI_OK;
+}
+
+eri_status eri_schwarz(const eri_plan* p, double* Q) {
+  g_err.clear();
+  if (!p || !Q) return fail(ERI_ERR_ARG, "plan or Q is NULL");
+  memcpy(Q, p->Q.data(), sizeof(double) * p->Q.size());
+  return ERI_OK;
+}
+
+eri_status eri_rys_roots(int N, int n, const double* T, double* u, double* w) {
+  g_err.clear();
+  if (N < 1 || N > RYS_NMAX) return fail(ERI_ERR_ARG, "N = %d outside [1, 9]", N);
+  if (n < 0 || (n > 0 && (!T || !u || !w))) return fail(ERI_ERR_ARG, "bad sizes or NULL arrays");
+  for (int t = 0; t < n; ++t)
+    if (!(T[t] >= 0) || !std::isfinite(T[t])) return fail(ERI_ERR_ARG, "T[%d] must be finite and >= 0", t);
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+    cudaGetLastError();
+    return fail(ERI_ERR_NO_DEVICE, "no CUDA device is visible");
+  }
+  if (n == 0) return ERI_OK;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  DeviceState* ds = nullptr;
+  eri_status s = device_init(dev, &ds);
+  if (s != ERI_OK) return s;
+  double *dT = nullptr, *du = nullptr, *dw = nullptr;
+  CUDA_TRY(cudaMalloc(&dT, sizeof(double) * n));
+  if (cudaMalloc(&du, sizeof(double) * n * N) != cudaSuccess || cudaMalloc(&dw, sizeof(double) * n * N) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(dT); cudaFree(du); cudaFree(dw);
+    return fail(ERI_ERR_OOM, "device allocation failed");
+  }
+  cudaError_t e = cudaMemcpy(dT, T, sizeof(double) * n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = (cudaError_t)erik_launch_rys(N, n, dT, du, dw, ds->rys_coef + RYS_COEF_OFFSET[N], ds->rys_au + RYS_ASYM_OFFSET[N],
+                                     ds->rys_aw + RYS_ASYM_OFFSET[N], RYS_TCUT[N], nullptr);
+  if (e == cudaSuccess) e = cudaMemcpy(u, du, sizeof(double) * n * N, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(w, dw, sizeof(double) * n * N, cudaMemcpyDeviceToHost);
+  cudaFree(dT); cudaFree(du); cudaFree(dw);
+  if (e != cudaSuccess) return fail(ERI_ERR_CUDA, "eri_rys_roots: %s", cudaGetErrorString(e));
+  return ERI_OK;
+}
+
+eri_status eri_flop_stats(eri_plan* p, eri_stats* out) {
+  g_err.clear();
+  if (!p || !out) return fail(ERI_ERR_ARG, "plan or out is NULL");
+  CUDA_TRY(cudaStreamSynchronize(p->last_stream));
+  std::vector<unsigned long long> st(2 * 256);
+  CUDA_TRY(cudaMemcpy(st.data(), p->d_stats, sizeof(unsigned long long) * 2 * 256, cudaMemcpyDeviceToHost));
+  memset(out, 0, sizeof(*out));
+  out->quartets_candidate = p->last_candidates;
+  for (int X = 0; X < ERI_NPAIRTYPE; ++X)
+    for (int Y = 0; Y < ERI_NPAIRTYPE; ++Y) {
+      const unsigned long long q = st[2 * (X * ERI_NPAIRTYPE + Y)], pq = st[2 * (X * ERI_NPAIRTYPE + Y) + 1];
+      out->quartets_computed += (long long)q;
+      out->prim_quartets += (long long)pq;
+      double fp, fq;
+      class_model_flops(p->dev->classes[X][Y], p->last_nD, p->last_want, &fp, &fq);
+      out->model_flops += fp * (double)pq + fq * (double)q;
+    }
+  out->npairs_total = (int)p->pairs_all.size();
+  out->npairs_kept = p->npairs_kept;
+  out->nclasses_launched = p->last_nclasses;
+  return ERI_OK;
+}
+
+eri_status eri_probe_fma_peak(double* fp64_tflops, double* fp32_tflops) {
+  g_err.clear();
+  if (!fp64_tflops || !fp32_tflops) return fail(ERI_ERR_ARG, "NULL output");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+    cudaGetLastError();
+    return fail(ERI_ERR_NO_DEVICE, "no CUDA device is visible");
+  }
+  CUDA_TRY(erik_probe_fma(fp64_tflops, fp32_tflops));
+  return ERI_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,221 @@
+"""Thin ctypes binding of liberi (include/eri.h): argument marshalling only.
+
+Every step of the J/K build runs in the CUDA library; this module only passes
+pointers and sizes.  If the library is missing it raises instead of falling
+back to anything else.  Device buffers are torch tensors (torch provides the
+device memory and the current stream).
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+from .build import LIB, HERE
+
+ERI_OK, ERI_ERR_ARG, ERI_ERR_BASIS, ERI_ERR_OOM, ERI_ERR_CUDA, ERI_ERR_NO_DEVICE, ERI_ERR_TIMEOUT, \
+    ERI_ERR_UNSUPPORTED_L = range(8)
+ERI_FP64, ERI_MIXED = 0, 1
+ERI_WANT_J, ERI_WANT_K = 1, 2
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+
+
+class EriError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"liberi status {status}: {msg}")
+        self.status = status
+
+
+class eri_basis(ctypes.Structure):
+    _fields_ = [("natm", ctypes.c_int), ("coords", _dp), ("nshell", ctypes.c_int),
+                ("shell_atom", _ip), ("shell_l", _ip), ("shell_nprim", _ip), ("shell_off", _ip),
+                ("exps", _dp), ("coefs", _dp), ("normalise", ctypes.c_int)]
+
+
+class eri_opts(ctypes.Structure):
+    _fields_ = [("screen_thresh", ctypes.c_double), ("precision", ctypes.c_int),
+                ("mixed_thresh", ctypes.c_double), ("max_nd", ctypes.c_int)]
+
+
+class eri_stats(ctypes.Structure):
+    _fields_ = [("quartets_candidate", ctypes.c_longlong), ("quartets_computed", ctypes.c_longlong),
+                ("prim_quartets", ctypes.c_longlong), ("quartets_fp32", ctypes.c_longlong),
+                ("model_flops", ctypes.c_double), ("npairs_total", ctypes.c_int),
+                ("npairs_kept", ctypes.c_int), ("nclasses_launched", ctypes.c_int)]
+
+
+_lib = None
+
+# name -> (restype, argtypes)
+_SIGS = {
+    "eri_plan_create": (ctypes.c_int, [ctypes.POINTER(eri_basis), ctypes.POINTER(eri_opts), ctypes.c_void_p,
+                                       ctypes.POINTER(ctypes.c_void_p)]),
+    "eri_plan_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "eri_plan_nbf": (ctypes.c_int, [ctypes.c_void_p]),
+    "eri_jk": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                              ctypes.c_int, ctypes.c_void_p]),
+    "eri_jk_host": (ctypes.c_int, [ctypes.c_void_p, _dp, ctypes.c_int, _dp, _dp, ctypes.c_int, ctypes.c_void_p]),
+    "eri_shell_quartet": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int] * 4 + [_dp]),
+    "eri_schwarz": (ctypes.c_int, [ctypes.c_void_p, _dp]),
+    "eri_rys_roots": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp]),
+    "eri_flop_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(eri_stats)]),
+    "eri_probe_fma_peak": (ctypes.c_int, [_dp, _dp]),
+    "eri_last_error": (ctypes.c_char_p, []),
+}
+
+
+def header_symbols():
+    """Function names declared in include/eri.h."""
+    path = os.path.join(HERE, "..", "include", "eri.h")
+    text = open(path).read()
+    return sorted(set(re.findall(r"^\s*(?:eri_status|int|const char\*)\s+(eri_\w+)\s*\(", text, re.M)))
+
+
+def load_library():
+    """Load the in-tree liberi.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            raise RuntimeError(f"{LIB} is missing: run build() first (no fallback exists)")
+        lib = ctypes.CDLL(LIB)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _check(status):
+    if status != ERI_OK:
+        raise EriError(status, load_library().eri_last_error().decode())
+
+
+def _d(a):
+    return a.ctypes.data_as(_dp)
+
+
+def _i(a):
+    return a.ctypes.data_as(_ip)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Plan:
+    """An eri_plan built from a molecule-like object (coords, shell_* arrays, exps, coefs)."""
+
+    def __init__(self, mol, tau=None, precision=ERI_FP64, mixed_thresh=1e-4, max_nd=8, normalise=True,
+                 stream=None):
+        lib = load_library()
+        self._arrs = dict(
+            coords=np.ascontiguousarray(mol.coords, dtype=np.float64),
+            atom=np.ascontiguousarray(mol.shell_atom, dtype=np.int32),
+            l=np.ascontiguousarray(mol.shell_l, dtype=np.int32),
+            nprim=np.ascontiguousarray(mol.shell_nprim, dtype=np.int32),
+            off=np.ascontiguousarray(mol.shell_off, dtype=np.int32),
+            exps=np.ascontiguousarray(mol.exps, dtype=np.float64),
+            coefs=np.ascontiguousarray(mol.coefs, dtype=np.float64),
+        )
+        A = self._arrs
+        self.nshell = int(A["l"].shape[0])
+        self.shell_l = A["l"]
+        b = eri_basis(int(A["coords"].shape[0]), _d(A["coords"]), self.nshell, _i(A["atom"]), _i(A["l"]),
+                      _i(A["nprim"]), _i(A["off"]), _d(A["exps"]), _d(A["coefs"]), 1 if normalise else 0)
+        if tau is None:
+            tau = getattr(mol, "tau", 1e-12)
+        o = eri_opts(float(tau), int(precision), float(mixed_thresh), int(max_nd))
+        h = ctypes.c_void_p()
+        st = ctypes.c_void_p(0) if stream is None else _stream_handle(stream)
+        _check(lib.eri_plan_create(ctypes.byref(b), ctypes.byref(o), st, ctypes.byref(h)))
+        self._h = h
+        self.nbf = lib.eri_plan_nbf(h)
+        self.max_nd = int(max_nd)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load_library().eri_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- device path
+    def jk(self, D, J=None, K=None, want=ERI_WANT_J | ERI_WANT_K, stream=None):
+        """J, K for CUDA float64 tensors D [nD, nbf, nbf] (or [nbf, nbf]); asynchronous."""
+        import torch
+        squeeze = D.dim() == 2
+        Dd = D.unsqueeze(0) if squeeze else D
+        if Dd.dtype != torch.float64 or not Dd.is_cuda or not Dd.is_contiguous():
+            raise ValueError("D must be a contiguous CUDA float64 tensor")
+        nD = Dd.shape[0]
+        if want & ERI_WANT_J and J is None:
+            J = torch.empty_like(Dd)
+        if want & ERI_WANT_K and K is None:
+            K = torch.empty_like(Dd)
+        _check(load_library().eri_jk(self._h, ctypes.c_void_p(Dd.data_ptr()), nD,
+                                     ctypes.c_void_p(J.data_ptr() if J is not None else 0),
+                                     ctypes.c_void_p(K.data_ptr() if K is not None else 0), want,
+                                     _stream_handle(stream)))
+        if squeeze:
+            J = J[0] if J is not None else None
+            K = K[0] if K is not None else None
+        return J, K
+
+    # -- host path (copies inside)
+    def jk_host(self, D, want=ERI_WANT_J | ERI_WANT_K, stream=0):
+        D = np.ascontiguousarray(D, dtype=np.float64)
+        squeeze = D.ndim == 2
+        if squeeze:
+            D = D[None]
+        J = np.zeros_like(D)
+        K = np.zeros_like(D)
+        st = ctypes.c_void_p(stream) if isinstance(stream, int) else _stream_handle(stream)
+        _check(load_library().eri_jk_host(self._h, _d(D), D.shape[0], _d(J), _d(K), want, st))
+        return (J[0], K[0]) if squeeze else (J, K)
+
+    def shell_quartet(self, i, j, k, l):
+        n = [(int(self.shell_l[s]) + 1) * (int(self.shell_l[s]) + 2) // 2 for s in (i, j, k, l)]
+        out = np.zeros(n)
+        _check(load_library().eri_shell_quartet(self._h, int(i), int(j), int(k), int(l), _d(out)))
+        return out
+
+    def schwarz(self):
+        Q = np.zeros((self.nshell, self.nshell))
+        _check(load_library().eri_schwarz(self._h, _d(Q)))
+        return Q
+
+    def stats(self):
+        s = eri_stats()
+        _check(load_library().eri_flop_stats(self._h, ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in eri_stats._fields_}
+
+
+def rys_roots(N, T):
+    """Device Rys roots u[len(T), N] and weights w[len(T), N]."""
+    T = np.ascontiguousarray(np.atleast_1d(T), dtype=np.float64)
+    u = np.zeros((T.size, N))
+    w = np.zeros((T.size, N))
+    _check(load_library().eri_rys_roots(int(N), int(T.size), _d(T), _d(u), _d(w)))
+    return u, w
+
+
+def probe_fma_peak():
+    """(FP64, FP32) FMA throughput of the current device in TFLOP/s, measured."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(load_library().eri_probe_fma_peak(ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value

@@ -1,0 +1,79 @@
+"""The C-ABI library builds for sm_103a, loads, exports every declared symbol and
+validates its arguments on the host (no GPU needed for these checks)."""
+
+import ctypes
+
+import numpy as np
+import pytest
+
+import paper_2407_09700_gb300 as pkg
+from paper_2407_09700_gb300 import eri as E
+from workloads import config_tiny
+
+
+@pytest.fixture(scope="module")
+def lib():
+    pkg.build()
+    return pkg.load_library()
+
+
+def test_exports_every_header_symbol(lib):
+    names = pkg.header_symbols()
+    assert len(names) >= 10
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def _basis(m):
+    arrs = dict(coords=np.ascontiguousarray(m.coords), atom=m.shell_atom.copy(), l=m.shell_l.copy(),
+                nprim=m.shell_nprim.copy(), off=m.shell_off.copy(), exps=m.exps.copy(), coefs=m.coefs.copy())
+    b = E.eri_basis(m.natm, E._d(arrs["coords"]), m.nshell, E._i(arrs["atom"]), E._i(arrs["l"]),
+                    E._i(arrs["nprim"]), E._i(arrs["off"]), E._d(arrs["exps"]), E._d(arrs["coefs"]), 1)
+    return b, arrs
+
+
+def _create(lib, b, opts):
+    h = ctypes.c_void_p()
+    return lib.eri_plan_create(ctypes.byref(b) if b is not None else None,
+                               ctypes.byref(opts) if opts is not None else None, None, ctypes.byref(h))
+
+
+def test_argument_validation_before_device(lib):
+    m = config_tiny()
+    b, keep = _basis(m)
+    good = E.eri_opts(1e-12, E.ERI_FP64, 1e-4, 1)
+    assert _create(lib, None, good) == E.ERI_ERR_ARG
+    assert _create(lib, b, None) == E.ERI_ERR_ARG
+    assert _create(lib, b, E.eri_opts(-1.0, 0, 1e-4, 1)) == E.ERI_ERR_ARG
+    assert _create(lib, b, E.eri_opts(1e-12, 0, 1e-4, 0)) == E.ERI_ERR_ARG
+    assert _create(lib, b, E.eri_opts(1e-12, 7, 1e-4, 1)) == E.ERI_ERR_ARG
+    keep["l"][2] = 5
+    assert _create(lib, b, good) == E.ERI_ERR_UNSUPPORTED_L
+    assert b"l = 5" in lib.eri_last_error()
+    keep["l"][2] = 1
+    keep["exps"][4] = -1.0
+    assert _create(lib, b, good) == E.ERI_ERR_BASIS
+    keep["exps"][4] = float("nan")
+    assert _create(lib, b, good) == E.ERI_ERR_BASIS
+    keep["exps"][4] = 0.5
+    keep["nprim"][0] = 0
+    assert _create(lib, b, good) == E.ERI_ERR_BASIS
+    keep["nprim"][0] = 3
+    keep["atom"][1] = 7
+    assert _create(lib, b, good) == E.ERI_ERR_BASIS
+    keep["atom"][1] = 0
+    # a well-formed request reaches the device check (or succeeds on a GPU machine)
+    rc = _create(lib, b, good)
+    assert rc in (E.ERI_OK, E.ERI_ERR_NO_DEVICE)
+
+
+def test_rys_and_jk_argument_checks(lib):
+    T = np.zeros(3)
+    u = np.zeros(30)
+    assert lib.eri_rys_roots(0, 3, E._d(T), E._d(u), E._d(u)) == E.ERI_ERR_ARG
+    assert lib.eri_rys_roots(10, 3, E._d(T), E._d(u), E._d(u)) == E.ERI_ERR_ARG
+    T[1] = -1.0
+    assert lib.eri_rys_roots(2, 3, E._d(T), E._d(u), E._d(u)) == E.ERI_ERR_ARG
+    assert lib.eri_jk(None, None, 1, None, None, 3, None) == E.ERI_ERR_ARG
+    assert lib.eri_plan_nbf(None) == -1
+    assert lib.eri_plan_destroy(None) == E.ERI_OK

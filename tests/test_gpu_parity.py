@@ -1,0 +1,158 @@
+"""Parity of the CUDA path (through the C-ABI) with the CPU oracle, on a GB300.
+
+Tolerances: shell-quartet blocks 1e-12 relative to the block's largest value
+(or 1e-13 absolute); J and K 1e-10 absolute (the FP64 path's bar).  Rys
+roots / weights are checked by the moment identity against the oracle's
+pinned Boys function.
+"""
+
+import itertools
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+import paper_2407_09700_gb300 as pkg  # noqa: E402
+from workloads import config_high_l, config_medium, config_tiny, custom_molecule, random_psd_density  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    pkg.build()
+    pkg.load_library()
+
+
+def _mixed_molecule(seed=0, natm=3, lmax=4, kmax=2, spread=1.6):
+    rng = np.random.default_rng(seed)
+    coords = rng.uniform(-spread, spread, (natm, 3))
+    shells = []
+    for a in range(natm):
+        for l in range(lmax + 1):
+            K = int(rng.integers(1, kmax + 1))
+            e = np.sort(rng.uniform(0.2, 3.0, K))[::-1]
+            shells.append((a, l, e, rng.uniform(0.2, 1.0, K)))
+    m = custom_molecule(coords, shells)
+    m.D = random_psd_density(m.nbf, max(2, m.nbf // 4), rng, nD=2)
+    return m
+
+
+# ---------------------------------------------------------------- Rys quadrature on the device
+
+@pytest.mark.parametrize("N", range(1, 10))
+def test_device_rys_moment_identity(N):
+    Ts = np.concatenate([[0.0, 1e-9, 0.5, 1.0, 3.3, 9.99, 17.0, 29.5], np.linspace(35, 120, 9), [400.0, 5e4]])
+    u, w = pkg.rys_roots(N, Ts)
+    for t, T in enumerate(Ts):
+        F = oracle.boys(2 * N - 1, float(T))
+        assert np.all(np.diff(u[t]) > 0) and np.all(w[t] > 0)
+        for k in range(2 * N):
+            got = float(np.dot(w[t], u[t] ** k))
+            assert abs(got - F[k]) <= 3e-14 * F[k], (N, T, k, got, F[k])
+
+
+# ---------------------------------------------------------------- single shell quartets
+
+def test_shell_quartets_every_class_up_to_g():
+    m = _mixed_molecule(seed=1, natm=2, lmax=4, kmax=2)
+    ob = oracle.OracleBasis(m)
+    plan = pkg.Plan(m, tau=0.0)
+    ns = m.nshell
+    # every (la, lb, lc, ld) combination appears; include non-canonical orders too
+    seen = set()
+    rng = np.random.default_rng(0)
+    quartets = []
+    for i, j, k, l in itertools.product(range(ns), repeat=4):
+        key = (int(m.shell_l[i]), int(m.shell_l[j]), int(m.shell_l[k]), int(m.shell_l[l]))
+        if key not in seen:
+            seen.add(key)
+            quartets.append((i, j, k, l))
+    assert len(seen) == 5 ** 4
+    worst = 0.0
+    for (i, j, k, l) in quartets:
+        g = plan.shell_quartet(i, j, k, l)
+        r = oracle.shell_quartet(ob, i, j, k, l)
+        err = np.abs(g - r).max()
+        scale = np.abs(r).max()
+        worst = max(worst, err / max(scale, 1e-300))
+        assert err <= 1e-12 * scale + 1e-13, ((i, j, k, l), err, scale)
+
+
+def test_schwarz_factors_match_oracle():
+    m = _mixed_molecule(seed=2, natm=3, lmax=3, kmax=3)
+    plan = pkg.Plan(m, tau=0.0)
+    np.testing.assert_allclose(plan.schwarz(), oracle.schwarz(m), rtol=1e-12, atol=1e-14)
+
+
+# ---------------------------------------------------------------- J / K builds
+
+def _jk_gpu(plan, D, want=3):
+    Dd = torch.from_numpy(np.ascontiguousarray(D)).cuda()
+    J, K = plan.jk(Dd, want=want)
+    torch.cuda.synchronize()
+    return (J.cpu().numpy() if J is not None else None), (K.cpu().numpy() if K is not None else None)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_jk_tiny(seed):
+    m = config_tiny(seed=seed)
+    plan = pkg.Plan(m)
+    J, K = _jk_gpu(plan, m.D)
+    Jr, Kr, n = oracle.jk(m)
+    assert np.abs(J - Jr).max() <= 1e-10
+    assert np.abs(K - Kr).max() <= 1e-10
+    st = plan.stats()
+    assert st["quartets_computed"] == n
+
+
+def test_jk_mixed_l_two_densities():
+    m = _mixed_molecule(seed=3, natm=3, lmax=4, kmax=2)
+    plan = pkg.Plan(m)
+    J, K = _jk_gpu(plan, m.D)
+    Jr, Kr, _ = oracle.jk(m)
+    assert np.abs(J - Jr).max() <= 1e-10, np.abs(J - Jr).max()
+    assert np.abs(K - Kr).max() <= 1e-10, np.abs(K - Kr).max()
+    assert np.abs(J - np.transpose(J, (0, 2, 1))).max() == 0.0
+
+
+def test_jk_flags_and_host_path():
+    m = _mixed_molecule(seed=4, natm=2, lmax=2, kmax=3)
+    plan = pkg.Plan(m)
+    Jr, Kr, _ = oracle.jk(m)
+    J, _ = _jk_gpu(plan, m.D, want=pkg.ERI_WANT_J)
+    _, K = _jk_gpu(plan, m.D, want=pkg.ERI_WANT_K)
+    assert np.abs(J - Jr).max() <= 1e-10 and np.abs(K - Kr).max() <= 1e-10
+    Jh, Kh = plan.jk_host(m.D)
+    assert np.abs(Jh - Jr).max() <= 1e-10 and np.abs(Kh - Kr).max() <= 1e-10
+
+
+def test_jk_everything_screened():
+    m = config_tiny(seed=0)
+    plan = pkg.Plan(m, tau=1e6)
+    J, K = _jk_gpu(plan, m.D)
+    assert np.all(J == 0) and np.all(K == 0)
+    assert plan.stats()["npairs_kept"] == 0
+
+
+def test_jk_medium_reduced():
+    # the medium recipe (3s2p1d per atom, depths 1..6) on 4 atoms: several tiles and ragged tails
+    m = config_medium(seed=5, natm=4)
+    plan = pkg.Plan(m)
+    J, K = _jk_gpu(plan, m.D)
+    Jr, Kr, _ = oracle.jk(m)
+    assert np.abs(J - Jr).max() <= 1e-10, np.abs(J - Jr).max()
+    assert np.abs(K - Kr).max() <= 1e-10, np.abs(K - Kr).max()
+
+
+def test_jk_high_l_reduced():
+    m = config_high_l(seed=6, natm=2, nocc=20)
+    plan = pkg.Plan(m)
+    J, K = _jk_gpu(plan, m.D)
+    Jr, Kr, _ = oracle.jk(m)
+    assert np.abs(J - Jr).max() <= 1e-10, np.abs(J - Jr).max()
+    assert np.abs(K - Kr).max() <= 1e-10, np.abs(K - Kr).max()
