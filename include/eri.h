@@ -135,6 +135,24 @@ eri_status eri_schwarz(const eri_plan* plan, double* Q);
  */
 eri_status eri_rys_roots(int N, int n, const double* T, double* u, double* w);
 
+/* Per-launch record of the last eri_jk call when profiling is on. */
+typedef struct {
+  int la, lb, lc, ld;             /* class of the launch */
+  int team_size;                  /* threads per shell quartet (1, 8 or 32) */
+  int grid;                       /* blocks launched */
+  float ms;                       /* CUDA-event time of the launch on the call's stream */
+  long long quartets;             /* shell quartets evaluated (after screening) */
+  long long prim_quartets;        /* primitive quartets evaluated */
+  double model_flops;             /* FP64 arithmetic of the launch by the kernel's operation count */
+} eri_launch_record;
+
+/* Turn per-launch CUDA-event timing of later eri_jk calls on (1) or off (0). */
+eri_status eri_set_profiling(eri_plan* plan, int enable);
+
+/* Records of the last eri_jk call (synchronises its stream): writes up to cap records to
+ * out (HOST) and the number available to *n.  Requires profiling to have been on. */
+eri_status eri_launch_records(eri_plan* plan, eri_launch_record* out, int cap, int* n);
+
 /* Counters of the last eri_jk call (synchronises that call's stream). */
 eri_status eri_flop_stats(eri_plan* plan, eri_stats* out);
 

@@ -18,6 +18,7 @@ from .oracle import (  # noqa: F401
     schwarz,
     jk,
     jk_blocks,
+    jk_sample,
     count_quartets,
     max_threads,
     OracleBasis,

@@ -387,10 +387,38 @@ int oracle_nbf(const obasis* bs) {
 static const int PERMS[8][4] = {{0, 1, 2, 3}, {1, 0, 2, 3}, {0, 1, 3, 2}, {1, 0, 3, 2},
                                 {2, 3, 0, 1}, {3, 2, 0, 1}, {2, 3, 1, 0}, {3, 2, 1, 0}};
 
-/* Full J/K.  screen: 0 = every unique quartet, 1 = the screening predicate.
- * Returns the number of unique shell quartets evaluated. */
-long long oracle_jk(const obasis* bs, int nD, const double* Dm, double* Jout, double* Kout,
-                    double tau, int screen) {
+/* Evaluate one unique shell quartet (I >= J, K >= L, pair IJ >= pair KL) and add every
+ * distinct ordered shell quartet of its orbit to J and K by the definitions. */
+static void unique_quartet_jk(const obasis* bs, const int* f0, int nbf, int nD, const double* Dm,
+                              double* Jl, double* Kl, double* g, int I, int J, int K, int L) {
+  int sh[4] = {I, J, K, L};
+  oracle_shell_quartet(bs, I, J, K, L, g);
+  int seen[8][4], nseen = 0;
+  for (int t = 0; t < 8; ++t) {
+    int o[4] = {sh[PERMS[t][0]], sh[PERMS[t][1]], sh[PERMS[t][2]], sh[PERMS[t][3]]};
+    int dup = 0;
+    for (int u = 0; u < nseen; ++u)
+      if (seen[u][0] == o[0] && seen[u][1] == o[1] && seen[u][2] == o[2] && seen[u][3] == o[3]) dup = 1;
+    if (dup) continue;
+    memcpy(seen[nseen++], o, sizeof(o));
+    digest_block(bs, f0, nbf, nD, Dm, Jl, Kl, sh, g, PERMS[t]);
+  }
+}
+
+static void pair_of(long long p, int* I, int* J) {
+  long long i = (long long)((sqrt(8.0 * (double)p + 1.0) - 1.0) * 0.5);
+  while (i * (i + 1) / 2 > p) --i;
+  while ((i + 1) * (i + 2) / 2 <= p) ++i;
+  *I = (int)i;
+  *J = (int)(p - i * (i + 1) / 2);
+}
+
+/* J/K over the unique quartets listed in qidx (all of them when qidx is NULL and nq < 0).
+ * A unique quartet's linear index u enumerates pairs of shell pairs p >= q with
+ * u = p (p + 1) / 2 + q and p = I (I + 1) / 2 + J (I >= J).  screen: 0 = none,
+ * 1 = the predicate.  Returns the number of quartets evaluated. */
+static long long jk_core(const obasis* bs, int nD, const double* Dm, double* Jout, double* Kout,
+                         double tau, int screen, const long long* qidx, long long nq) {
   int nsh = bs->nshell, nbf = oracle_nbf(bs), mb = max_block(bs);
   int* f0 = (int*)malloc(sizeof(int) * nsh);
   first_bf(bs, f0);
@@ -400,38 +428,31 @@ long long oracle_jk(const obasis* bs, int nD, const double* Dm, double* Jout, do
   size_t mat = (size_t)nD * nbf * nbf;
   memset(Jout, 0, sizeof(double) * mat);
   memset(Kout, 0, sizeof(double) * mat);
-  int npair = nsh * (nsh + 1) / 2;
+  long long npair = (long long)nsh * (nsh + 1) / 2;
+  long long total = qidx ? nq : npair * (npair + 1) / 2;
   long long count = 0;
 #pragma omp parallel reduction(+ : count)
   {
     double* Jl = (double*)calloc(mat, sizeof(double));
     double* Kl = (double*)calloc(mat, sizeof(double));
     double* g = (double*)malloc(sizeof(double) * (size_t)mb * mb * mb * mb);
-#pragma omp for schedule(dynamic)
-    for (int p = 0; p < npair; ++p) {
-      int I = 0;
-      while ((I + 1) * (I + 2) / 2 <= p) ++I;
-      int J = p - I * (I + 1) / 2;
-      for (int q = 0; q <= p; ++q) {
-        int K = 0;
-        while ((K + 1) * (K + 2) / 2 <= q) ++K;
-        int L = q - K * (K + 1) / 2;
-        if (screen && !keep_quartet(Q, Dmax, nsh, tau, I, J, K, L)) continue;
-        ++count;
-        int sh[4] = {I, J, K, L};
-        oracle_shell_quartet(bs, I, J, K, L, g);
-        /* expand every distinct ordered shell quartet of the orbit */
-        int seen[8][4], nseen = 0;
-        for (int t = 0; t < 8; ++t) {
-          int o[4] = {sh[PERMS[t][0]], sh[PERMS[t][1]], sh[PERMS[t][2]], sh[PERMS[t][3]]};
-          int dup = 0;
-          for (int u = 0; u < nseen; ++u)
-            if (seen[u][0] == o[0] && seen[u][1] == o[1] && seen[u][2] == o[2] && seen[u][3] == o[3]) dup = 1;
-          if (dup) continue;
-          memcpy(seen[nseen++], o, sizeof(o));
-          digest_block(bs, f0, nbf, nD, Dm, Jl, Kl, sh, g, PERMS[t]);
-        }
+#pragma omp for schedule(dynamic, 16)
+    for (long long t = 0; t < total; ++t) {
+      long long u = qidx ? qidx[t] : t;
+      int I, J, K, L;
+      long long p, q;
+      {
+        long long i = (long long)((sqrt(8.0 * (double)u + 1.0) - 1.0) * 0.5);
+        while (i * (i + 1) / 2 > u) --i;
+        while ((i + 1) * (i + 2) / 2 <= u) ++i;
+        p = i;
+        q = u - i * (i + 1) / 2;
       }
+      pair_of(p, &I, &J);
+      pair_of(q, &K, &L);
+      if (screen && !keep_quartet(Q, Dmax, nsh, tau, I, J, K, L)) continue;
+      ++count;
+      unique_quartet_jk(bs, f0, nbf, nD, Dm, Jl, Kl, g, I, J, K, L);
     }
 #pragma omp critical
     {
@@ -441,6 +462,20 @@ long long oracle_jk(const obasis* bs, int nD, const double* Dm, double* Jout, do
   }
   free(f0); free(Q); free(Dmax);
   return count;
+}
+
+/* Full J/K.  screen: 0 = every unique quartet, 1 = the screening predicate.
+ * Returns the number of unique shell quartets evaluated. */
+long long oracle_jk(const obasis* bs, int nD, const double* Dm, double* Jout, double* Kout,
+                    double tau, int screen) {
+  return jk_core(bs, nD, Dm, Jout, Kout, tau, screen, NULL, -1);
+}
+
+/* Partial J/K over a list of unique-quartet indices (see jk_core); used to time the
+ * oracle on a bounded random sample of a large build. */
+long long oracle_jk_sample(const obasis* bs, int nD, const double* Dm, double* Jout, double* Kout,
+                           double tau, int screen, const long long* qidx, long long nq) {
+  return jk_core(bs, nD, Dm, Jout, Kout, tau, screen, qidx, nq);
 }
 
 /* Sampled blocks for large inputs, straight from the definitions with no symmetry:

@@ -60,6 +60,10 @@ def _get():
         lib.oracle_jk.restype = ctypes.c_longlong
         lib.oracle_jk_blocks.argtypes = [ctypes.POINTER(_OBasis), ctypes.c_int, _dp, ctypes.c_int,
                                          _ip, _dp, _dp, ctypes.c_double, ctypes.c_int]
+        lib.oracle_jk_sample.argtypes = [ctypes.POINTER(_OBasis), ctypes.c_int, _dp, _dp, _dp,
+                                         ctypes.c_double, ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_longlong), ctypes.c_longlong]
+        lib.oracle_jk_sample.restype = ctypes.c_longlong
         lib.oracle_count_quartets.argtypes = [ctypes.POINTER(_OBasis), ctypes.c_int, _dp,
                                               ctypes.c_double, ctypes.c_int]
         lib.oracle_count_quartets.restype = ctypes.c_longlong
@@ -188,6 +192,21 @@ def jk_blocks(mol, pairs, D=None, tau=None, screen: bool = True):
         Jl.append(Jb[s, :, : ni * nx].reshape(nD, ni, nx))
         Kl.append(Kb[s, :, : ni * nx].reshape(nD, ni, nx))
     return Jl, Kl
+
+
+def jk_sample(mol, qidx, D=None, tau=None, screen: bool = True):
+    """Partial J/K over the listed unique-quartet indices (u = p(p+1)/2 + q, p >= q,
+    p = I(I+1)/2 + J with I >= J).  Returns (J, K, n_evaluated)."""
+    b = _basis(mol)
+    D = _dens(mol, D)
+    if tau is None:
+        tau = getattr(mol, "tau", 1e-12)
+    q = np.ascontiguousarray(np.asarray(qidx, dtype=np.int64))
+    J = np.zeros_like(D)
+    K = np.zeros_like(D)
+    n = _get().oracle_jk_sample(b.ptr(), D.shape[0], _d(D), _d(J), _d(K), float(tau), 1 if screen else 0,
+                                q.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)), int(q.size))
+    return J, K, int(n)
 
 
 def count_quartets(mol, D=None, tau=None, screen: bool = True) -> int:

@@ -267,6 +267,11 @@ struct eri_plan {
   // last eri_jk bookkeeping
   long long last_candidates = 0;
   int last_nclasses = 0, last_nD = 1, last_want = 3;
+  // optional per-launch timing
+  bool profiling = false;
+  std::vector<cudaEvent_t> events;            // 2 per launch
+  std::vector<int> last_launch_xy;            // X*15+Y per launch
+  std::vector<int> last_launch_ts, last_launch_grid;
 };
 
 namespace {
@@ -400,6 +405,7 @@ eri_status eri_plan_destroy(eri_plan* p) {
   if (!p) return ERI_OK;
   cudaSetDevice(p->device);
   cudaDeviceSynchronize();
+  for (cudaEvent_t e : p->events) cudaEventDestroy(e);
   void* bufs[] = {p->d_pairs_all, p->d_pairs, p->d_prims, p->d_sh_bf0, p->d_sh_n, p->d_Dmax, p->d_counters,
                   p->d_stats, p->d_scratch, p->d_tasks, p->d_out, p->d_off, p->d_host_io};
   for (void* b : bufs)
@@ -605,6 +611,16 @@ eri_status eri_jk(eri_plan* p, const double* D, int nD, double* J, double* K, in
   }
   eri_status s = ensure_scratch(p, need);
   if (s != ERI_OK) return s;
+  if (p->profiling) {
+    while (p->events.size() < 2 * launches.size()) {
+      cudaEvent_t e;
+      CUDA_TRY(cudaEventCreate(&e));
+      p->events.push_back(e);
+    }
+  }
+  p->last_launch_xy.clear();
+  p->last_launch_ts.clear();
+  p->last_launch_grid.clear();
   int li = 0;
   for (const L& l : launches) {
     KernelArgs a = base_args(p, l.X, l.Y);
@@ -626,7 +642,12 @@ eri_status eri_jk(eri_plan* p, const double* D, int nD, double* J, double* K, in
     a.counter = p->d_counters + li;
     a.scratch = p->d_scratch;
     a.stats = p->d_stats + 2 * (l.X * ERI_NPAIRTYPE + l.Y);
+    if (p->profiling) CUDA_TRY(cudaEventRecord(p->events[2 * li], st));
     CUDA_TRY(erik_launch_class(l.ts, &a, l.grid, l.smem, st));
+    if (p->profiling) CUDA_TRY(cudaEventRecord(p->events[2 * li + 1], st));
+    p->last_launch_xy.push_back(l.X * ERI_NPAIRTYPE + l.Y);
+    p->last_launch_ts.push_back(l.ts);
+    p->last_launch_grid.push_back(l.grid);
     ++li;
   }
   if (want & 1) CUDA_TRY(erik_launch_symmetrize(J, nD, p->nbf, st));
@@ -760,6 +781,42 @@ eri_status eri_flop_stats(eri_plan* p, eri_stats* out) {
   out->npairs_total = (int)p->pairs_all.size();
   out->npairs_kept = p->npairs_kept;
   out->nclasses_launched = p->last_nclasses;
+  return ERI_OK;
+}
+
+eri_status eri_set_profiling(eri_plan* p, int enable) {
+  g_err.clear();
+  if (!p) return fail(ERI_ERR_ARG, "plan is NULL");
+  p->profiling = enable != 0;
+  return ERI_OK;
+}
+
+eri_status eri_launch_records(eri_plan* p, eri_launch_record* out, int cap, int* n) {
+  g_err.clear();
+  if (!p || !n || (cap > 0 && !out)) return fail(ERI_ERR_ARG, "NULL argument");
+  if (!p->profiling) return fail(ERI_ERR_ARG, "profiling is off for this plan");
+  CUDA_TRY(cudaStreamSynchronize(p->last_stream));
+  const int nl = (int)p->last_launch_xy.size();
+  *n = nl;
+  if (nl == 0) return ERI_OK;
+  std::vector<unsigned long long> st(2 * 256);
+  CUDA_TRY(cudaMemcpy(st.data(), p->d_stats, sizeof(unsigned long long) * 2 * 256, cudaMemcpyDeviceToHost));
+  for (int i = 0; i < nl && i < cap; ++i) {
+    const int xy = p->last_launch_xy[i];
+    const ClassDesc& c = p->dev->classes[xy / ERI_NPAIRTYPE][xy % ERI_NPAIRTYPE];
+    eri_launch_record& r = out[i];
+    r.la = c.la; r.lb = c.lb; r.lc = c.lc; r.ld = c.ld;
+    r.team_size = p->last_launch_ts[i];
+    r.grid = p->last_launch_grid[i];
+    float ms = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&ms, p->events[2 * i], p->events[2 * i + 1]));
+    r.ms = ms;
+    r.quartets = (long long)st[2 * xy];
+    r.prim_quartets = (long long)st[2 * xy + 1];
+    double fp, fq;
+    class_model_flops(c, p->last_nD, p->last_want, &fp, &fq);
+    r.model_flops = fp * (double)r.prim_quartets + fq * (double)r.quartets;
+  }
   return ERI_OK;
 }
 

@@ -49,6 +49,13 @@ class eri_stats(ctypes.Structure):
                 ("npairs_kept", ctypes.c_int), ("nclasses_launched", ctypes.c_int)]
 
 
+class eri_launch_record(ctypes.Structure):
+    _fields_ = [("la", ctypes.c_int), ("lb", ctypes.c_int), ("lc", ctypes.c_int), ("ld", ctypes.c_int),
+                ("team_size", ctypes.c_int), ("grid", ctypes.c_int), ("ms", ctypes.c_float),
+                ("quartets", ctypes.c_longlong), ("prim_quartets", ctypes.c_longlong),
+                ("model_flops", ctypes.c_double)]
+
+
 _lib = None
 
 # name -> (restype, argtypes)
@@ -65,6 +72,9 @@ _SIGS = {
     "eri_rys_roots": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp]),
     "eri_flop_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(eri_stats)]),
     "eri_probe_fma_peak": (ctypes.c_int, [_dp, _dp]),
+    "eri_set_profiling": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "eri_launch_records": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(eri_launch_record), ctypes.c_int,
+                                          ctypes.POINTER(ctypes.c_int)]),
     "eri_last_error": (ctypes.c_char_p, []),
 }
 
@@ -198,6 +208,16 @@ class Plan:
         Q = np.zeros((self.nshell, self.nshell))
         _check(load_library().eri_schwarz(self._h, _d(Q)))
         return Q
+
+    def set_profiling(self, on=True):
+        _check(load_library().eri_set_profiling(self._h, 1 if on else 0))
+
+    def launch_records(self):
+        """Per-launch records of the last jk call (class, team size, ms, counts, model FLOPs)."""
+        arr = (eri_launch_record * 256)()
+        n = ctypes.c_int()
+        _check(load_library().eri_launch_records(self._h, arr, 256, ctypes.byref(n)))
+        return [{k: getattr(arr[i], k) for k, _ in eri_launch_record._fields_} for i in range(n.value)]
 
     def stats(self):
         s = eri_stats()

@@ -265,3 +265,19 @@ def test_screening_predicate_effect():
     _, _, nbig = oracle.jk(b, tau=1e6, screen=True)
     assert nbig == 0
     assert oracle.count_quartets(b, tau=0.0, screen=True) == n0
+
+
+def test_sampled_jk_partitions_the_full_build():
+    # the unique quartets split into two disjoint samples add up to the full build
+    m = config_tiny(seed=3)
+    b = oracle.OracleBasis(m)
+    J, K, n = oracle.jk(b, screen=True)
+    npair = m.nshell * (m.nshell + 1) // 2
+    allq = np.arange(npair * (npair + 1) // 2)
+    rng = np.random.default_rng(0)
+    rng.shuffle(allq)
+    half = allq.size // 2
+    J1, K1, n1 = oracle.jk_sample(b, allq[:half])
+    J2, K2, n2 = oracle.jk_sample(b, allq[half:])
+    assert n1 + n2 == n
+    assert np.abs(J1 + J2 - J).max() <= 1e-13 and np.abs(K1 + K2 - K).max() <= 1e-13
