@@ -111,6 +111,29 @@ eri_status eri_jk(eri_plan* plan, const double* D, int nD, double* J, double* K,
                   void* cuda_stream);
 
 /*
+ * eri_jk for callers that cannot allocate device memory during the call.  The
+ * paper has no counterpart; this is a library convenience.  eri_jk may grow
+ * the plan's scratch with cudaMalloc (after synchronising the device) the
+ * first time a larger class is launched; code inside CUDA stream capture, in a
+ * host callback, or under an allocator that owns all device memory cannot
+ * allow that.  This call allocates nothing and calls no cudaMalloc / cudaFree
+ * or allocating library routine: the class kernels' scratch is a file-scope
+ * static device array of 32 MiB (ERI_NOALLOC_SCRATCH_BYTES) that every GPU
+ * loading the library holds until the process exits.  Arguments, layout and
+ * results are those of eri_jk (D, J, K device pointers; J and K overwritten).
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  Every call shares the one array, and nothing in it needs to start
+ * at zero (each value is written before it is read in the same call); calls
+ * that overlap on the GPU, on any plan, race on it.  A class launch uses as
+ * many blocks as the array can hold; a class whose single block needs more
+ * scratch than the array is rejected with ERI_ERR_ARG before any launch.
+ * The plan must belong to the current device (ERI_ERR_ARG otherwise).
+ */
+eri_status eri_jk_noalloc(eri_plan* plan, const double* D, int nD, double* J, double* K, int flags,
+                          void* cuda_stream);
+
+/*
  * Same as eri_jk, with D, J and K in HOST memory: copies D to the device,
  * builds J/K and copies them back.  Synchronous.
  */

@@ -833,3 +833,89 @@ eri_status eri_probe_fma_peak(double* fp64_tflops, double* fp32_tflops) {
 }
 
 }  // extern "C"
+
+// ================================================================= internal hooks for eri_noalloc.cu
+// Record a failure for eri_last_error() from another translation unit.
+extern "C" __attribute__((visibility("hidden"))) eri_status eri_internal_fail(eri_status s, const char* msg) {
+  return fail(s, "%s", msg);
+}
+
+// The J/K build of eri_jk with caller-provided team scratch of a fixed size: nothing is
+// allocated.  Each class launch uses as many blocks as its scratch need allows (at most the
+// occupancy-limited grid); a class whose single block needs more than scratch_doubles is
+// rejected with ERI_ERR_ARG before anything is launched.
+extern "C" __attribute__((visibility("hidden"))) eri_status eri_internal_jk_fixed_scratch(
+    eri_plan* p, const double* D, int nD, double* J, double* K,
+                                                    int flags, void* cuda_stream, double* scratch,
+                                                    size_t scratch_doubles) {
+  g_err.clear();
+  if (!p) return fail(ERI_ERR_ARG, "plan is NULL");
+  if (!D) return fail(ERI_ERR_ARG, "D is NULL");
+  if (nD < 1 || nD > p->opts.max_nd) return fail(ERI_ERR_ARG, "nD = %d outside [1, %d]", nD, p->opts.max_nd);
+  const int want = flags & 3;
+  if (want == 0) return fail(ERI_ERR_ARG, "flags request neither J nor K");
+  if ((want & 1) && !J) return fail(ERI_ERR_ARG, "J requested but NULL");
+  if ((want & 2) && !K) return fail(ERI_ERR_ARG, "K requested but NULL");
+  int cur = -1;
+  CUDA_TRY(cudaGetDevice(&cur));
+  if (cur != p->device) return fail(ERI_ERR_ARG, "the plan belongs to device %d but device %d is current", p->device, cur);
+  struct L { int X, Y, grid, smem, ts; long long nt; };
+  std::vector<L> launches;
+  long long cand = 0;
+  for (int X = 0; X < ERI_NPAIRTYPE; ++X) {
+    if (!p->type_cnt[X]) continue;
+    for (int Y = 0; Y <= X; ++Y) {
+      if (!p->type_cnt[Y]) continue;
+      const long long nx = p->type_cnt[X], ny = p->type_cnt[Y];
+      const long long nt = (X == Y) ? nx * (nx + 1) / 2 : nx * ny;
+      L l{X, Y, 0, 0, 0, nt};
+      eri_status s = launch_shape(p, X, Y, nt, &l.grid, &l.smem, &l.ts);
+      if (s != ERI_OK) return s;
+      const size_t per_block = (size_t)(128 / l.ts) * (size_t)p->dev->classes[X][Y].scratch_per_team;
+      if (per_block > scratch_doubles) {
+        const ClassDesc& c = p->dev->classes[X][Y];
+        return fail(ERI_ERR_ARG,
+                    "class (%d%d|%d%d) needs %zu bytes of scratch for one block, more than the %zu-byte "
+                    "static scratch of eri_jk_noalloc",
+                    c.la, c.lb, c.lc, c.ld, per_block * sizeof(double), scratch_doubles * sizeof(double));
+      }
+      l.grid = (int)std::min<size_t>((size_t)l.grid, scratch_doubles / per_block);
+      launches.push_back(l);
+      cand += nt;
+    }
+  }
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const size_t mat = (size_t)nD * p->nbf * p->nbf;
+  if (want & 1) CUDA_TRY(cudaMemsetAsync(J, 0, sizeof(double) * mat, st));
+  if (want & 2) CUDA_TRY(cudaMemsetAsync(K, 0, sizeof(double) * mat, st));
+  CUDA_TRY(erik_launch_dmax(D, nD, p->nbf, p->nshell, p->d_sh_bf0, p->d_sh_n, p->d_Dmax, st));
+  CUDA_TRY(cudaMemsetAsync(p->d_counters, 0, sizeof(unsigned long long) * 256, st));
+  CUDA_TRY(cudaMemsetAsync(p->d_stats, 0, sizeof(unsigned long long) * 2 * 256, st));
+  int li = 0;
+  for (const L& l : launches) {
+    KernelArgs a = base_args(p, l.X, l.Y);
+    a.pairs = p->d_pairs;
+    a.bra0 = p->type_off[l.X];
+    a.nbra = p->type_cnt[l.X];
+    a.ket0 = p->type_off[l.Y];
+    a.nket = p->type_cnt[l.Y];
+    a.tri = (l.X == l.Y);
+    a.ntask = l.nt;
+    a.Dmax = p->d_Dmax;
+    a.tau = p->opts.screen_thresh;
+    a.D = D;
+    a.J = J;
+    a.K = K;
+    a.nD = nD;
+    a.want = want;
+    a.mode = KMODE_JK;
+    a.counter = p->d_counters + li;
+    a.scratch = scratch;
+    a.stats = p->d_stats + 2 * (l.X * ERI_NPAIRTYPE + l.Y);
+    CUDA_TRY(erik_launch_class(l.ts, &a, l.grid, l.smem, st));
+    ++li;
+  }
+  if (want & 1) CUDA_TRY(erik_launch_symmetrize(J, nD, p->nbf, st));
+  if (want & 2) CUDA_TRY(erik_launch_symmetrize(K, nD, p->nbf, st));
+  return ERI_OK;
+}

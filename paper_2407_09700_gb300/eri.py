@@ -66,6 +66,8 @@ _SIGS = {
     "eri_plan_nbf": (ctypes.c_int, [ctypes.c_void_p]),
     "eri_jk": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                               ctypes.c_int, ctypes.c_void_p]),
+    "eri_jk_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                      ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "eri_jk_host": (ctypes.c_int, [ctypes.c_void_p, _dp, ctypes.c_int, _dp, _dp, ctypes.c_int, ctypes.c_void_p]),
     "eri_shell_quartet": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int] * 4 + [_dp]),
     "eri_schwarz": (ctypes.c_int, [ctypes.c_void_p, _dp]),
