@@ -8,12 +8,14 @@
 #define ERI_MAXCART 165           // Cartesian triples with l <= 8
 
 // One primitive pair (Gaussian product of Eq. 2's primitives on the pair's two
-// centres A, B).  64 bytes, 16-byte aligned, so a pair loads as four double2.
+// centres A, B).  80 bytes, 16-byte aligned.
 struct PrimPair {
   double zeta;     // alpha + beta
   double P[3];     // (alpha A + beta B) / zeta
   double PA[3];    // P - A
   double E;        // sqrt(2) pi^(5/4) / zeta * exp(-alpha beta |A-B|^2 / zeta) * c_alpha c_beta
+  double hz;       // 1 / (2 zeta)
+  double pad;
 };
 
 // One shell pair in canonical orientation (l of sh0 >= l of sh1).  64 bytes.
@@ -79,6 +81,7 @@ struct KernelArgs {
   const double* rys_au;
   const double* rys_aw;
   int rys_tcut;
+  double rys_tcut_d;           // the same cutoff as a double
 };
 
 // Host-side launchers implemented in eri_kernels.cu.  All return a cudaError_t as int.

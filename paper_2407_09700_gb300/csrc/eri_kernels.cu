@@ -54,11 +54,20 @@ __device__ __forceinline__ double horner12(const double* __restrict__ c, double 
   return a;
 }
 
+// floor(T) for 0 <= T < 2^30 using integer operations only (no FP64-pipe conversion)
+__device__ __forceinline__ int floor_nonneg(double T) {
+  const long long b = __double_as_longlong(T);
+  const int e = (int)((b >> 52) & 0x7ff) - 1023;
+  if (e < 0) return 0;
+  const long long m = (b & 0xfffffffffffffLL) | 0x10000000000000LL;
+  return (int)(m >> (52 - e));
+}
+
 // Prepare the table lookup for one T: ti >= 0 selects interval ti, else the large-T limit.
-__device__ __forceinline__ void rys_locate(double T, int tcut, int& ti, double& x, double& invT, double& rsqT) {
-  if (T < (double)tcut) {
-    ti = (int)T;
-    x = 2.0 * (T - (double)ti) - 1.0;
+__device__ __forceinline__ void rys_locate(double T, double tcut, int& ti, double& x, double& invT, double& rsqT) {
+  if (T < tcut) {
+    ti = floor_nonneg(T);
+    x = fma(2.0, T, -(double)(2 * ti + 1));
     invT = 0.0;
     rsqT = 0.0;
   } else {
@@ -83,39 +92,58 @@ __device__ __forceinline__ void rys_root(const double* __restrict__ coef, const 
 }
 
 // ------------------------------------------------------------------ 2D recurrences
-// I(n, m) for n <= Le, m <= Lf at g[n*(Lf+1) + m] (Sec. 2's RRs, Rys-Dupuis-King form):
+// I(n, m) for n <= Le, m <= Lf at g[o + n*(Lf+1) + m], for the x, y and z tables at once
+// (Sec. 2's RRs in the Rys-Dupuis-King form):
 //   I(n+1, 0) = C00 I(n, 0) + n B10 I(n-1, 0)
 //   I(n, m+1) = C00' I(n, m) + n B00 I(n-1, m) + m B01 I(n, m-1)
-__device__ __forceinline__ void rys_2d(const Smem& g, int o, int Le, int Lf, double I00, double C00,
-                                       double C00p, double B00, double B10, double B01) {
+// I_x(0,0) = I_y(0,0) = 1 and I_z(0,0) = w Theta.  The running multiples n B10, n B00 and
+// m B01 are shared by the three axes.
+__device__ __forceinline__ void rys_2d3(const Smem& g, const int o[3], int Le, int Lf, double I0z,
+                                        const double C[3], const double Cp[3], double B00, double B10,
+                                        double B01) {
   const int L1 = Lf + 1;
-  g[o] = I00;
-  if (Le >= 1) g[o + L1] = C00 * I00;
+  g[o[0]] = 1.0;
+  g[o[1]] = 1.0;
+  g[o[2]] = I0z;
+  if (Le >= 1) {
+    g[o[0] + L1] = C[0];
+    g[o[1] + L1] = C[1];
+    g[o[2] + L1] = C[2] * I0z;
+  }
   double nb10 = B10;
   for (int n = 1; n < Le; ++n) {
-    g[o + (n + 1) * L1] = fma(C00, g[o + n * L1], nb10 * g[o + (n - 1) * L1]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      g[o[a] + (n + 1) * L1] = fma(C[a], g[o[a] + n * L1], nb10 * g[o[a] + (n - 1) * L1]);
     nb10 += B10;
   }
   if (Lf == 0) return;
-  // m = 0 -> 1
-  {
-    g[o + 1] = C00p * g[o];
-    double nb00 = B00;
-    for (int n = 1; n <= Le; ++n) {
-      g[o + n * L1 + 1] = fma(C00p, g[o + n * L1], nb00 * g[o + (n - 1) * L1]);
-      nb00 += B00;
-    }
-  }
+  // row n = 0
+  g[o[0] + 1] = Cp[0];
+  g[o[1] + 1] = Cp[1];
+  g[o[2] + 1] = Cp[2] * I0z;
   double mb01 = B01;
   for (int m = 1; m < Lf; ++m) {
-    g[o + m + 1] = fma(C00p, g[o + m], mb01 * g[o + m - 1]);
-    double nb00 = B00;
-    for (int n = 1; n <= Le; ++n) {
-      const int e = o + n * L1 + m;
-      g[e + 1] = fma(C00p, g[e], fma(nb00, g[e - L1], mb01 * g[e - 1]));
-      nb00 += B00;
-    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) g[o[a] + m + 1] = fma(Cp[a], g[o[a] + m], mb01 * g[o[a] + m - 1]);
     mb01 += B01;
+  }
+  // rows n >= 1
+  double nb00 = B00;
+  for (int n = 1; n <= Le; ++n) {
+    const int r = n * L1;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) g[o[a] + r + 1] = fma(Cp[a], g[o[a] + r], nb00 * g[o[a] + r - L1]);
+    double mb = B01;
+    for (int m = 1; m < Lf; ++m) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const int e = o[a] + r + m;
+        g[e + 1] = fma(Cp[a], g[e], fma(nb00, g[e - L1], mb * g[e - 1]));
+      }
+      mb += B01;
+    }
+    nb00 += B00;
   }
 }
 
@@ -278,22 +306,23 @@ __global__ void __launch_bounds__(TPB) eri_class_kernel(const KernelArgs a) {
             const double T = zeta * rz * fma(PQ0, PQ0, fma(PQ1, PQ1, PQ2 * PQ2));
             int ti;
             double xx, invT, rsqT;
-            rys_locate(T, a.rys_tcut, ti, xx, invT, rsqT);
+            rys_locate(T, a.rys_tcut_d, ti, xx, invT, rsqT);
+            const double hz = x->hz, he = y->hz;
             const int o = S_PRIM + j * NPS;
             sm[o + 0] = x->PA[0]; sm[o + 1] = x->PA[1]; sm[o + 2] = x->PA[2];
             sm[o + 3] = y->PA[0]; sm[o + 4] = y->PA[1]; sm[o + 5] = y->PA[2];
             sm[o + 6] = rz * PQ0; sm[o + 7] = rz * PQ1; sm[o + 8] = rz * PQ2;
             sm[o + 9] = re * PQ0; sm[o + 10] = re * PQ1; sm[o + 11] = re * PQ2;
             sm[o + 12] = 0.5 * inv_s;
-            sm[o + 13] = 0.5 / zeta;
-            sm[o + 14] = 0.5 / eta;
-            sm[o + 15] = rz;
-            sm[o + 16] = re;
+            sm[o + 13] = hz;
+            sm[o + 14] = he;
+            sm[o + 15] = hz * rz;
+            sm[o + 16] = he * re;
             sm[o + 17] = x->E * y->E * r;           // Theta with contraction coefficients
             sm[o + 18] = xx;
             sm[o + 19] = invT;
             sm[o + 20] = rsqT;
-            sm[o + 21] = (double)ti;
+            sm[o + 21] = __longlong_as_double((long long)ti);
           }
         }
         __syncwarp();
@@ -303,18 +332,19 @@ __global__ void __launch_bounds__(TPB) eri_class_kernel(const KernelArgs a) {
           if (j < nbt) {
             const int o = S_PRIM + j * NPS;
             double u, w;
-            rys_root(a.rys_coef, a.rys_au, a.rys_aw, N, (int)sm[o + 21], sm[o + 18], sm[o + 19], sm[o + 20],
-                     n, u, w);
+            rys_root(a.rys_coef, a.rys_au, a.rys_aw, N, (int)__double_as_longlong(sm[o + 21]), sm[o + 18],
+                     sm[o + 19], sm[o + 20], n, u, w);
             const double B00 = u * sm[o + 12];
-            const double B10 = sm[o + 13] * fma(-u, sm[o + 15], 1.0);
-            const double B01 = sm[o + 14] * fma(-u, sm[o + 16], 1.0);
+            const double B10 = fma(-u, sm[o + 15], sm[o + 13]);
+            const double B01 = fma(-u, sm[o + 16], sm[o + 14]);
             const double wt = w * sm[o + 17];
+            const double C[3] = {fma(-u, sm[o + 6], sm[o + 0]), fma(-u, sm[o + 7], sm[o + 1]),
+                                 fma(-u, sm[o + 8], sm[o + 2])};
+            const double Cp[3] = {fma(u, sm[o + 9], sm[o + 3]), fma(u, sm[o + 10], sm[o + 4]),
+                                  fma(u, sm[o + 11], sm[o + 5])};
             const int g0 = S_2D + ((j * 3 + 0) * N + n) * nI;
-            const int g1 = g0 + N * nI;
-            const int g2 = g1 + N * nI;
-            rys_2d(sm, g0, Le, Lf, 1.0, fma(-u, sm[o + 6], sm[o + 0]), fma(u, sm[o + 9], sm[o + 3]), B00, B10, B01);
-            rys_2d(sm, g1, Le, Lf, 1.0, fma(-u, sm[o + 7], sm[o + 1]), fma(u, sm[o + 10], sm[o + 4]), B00, B10, B01);
-            rys_2d(sm, g2, Le, Lf, wt, fma(-u, sm[o + 8], sm[o + 2]), fma(u, sm[o + 11], sm[o + 5]), B00, B10, B01);
+            const int og[3] = {g0, g0 + N * nI, g0 + 2 * N * nI};
+            rys_2d3(sm, og, Le, Lf, wt, C, Cp, B00, B10, B01);
           }
         }
         __syncwarp();

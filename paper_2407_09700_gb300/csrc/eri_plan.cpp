@@ -182,17 +182,29 @@ eri_status device_init(int dev, DeviceState** out) {
   return ERI_OK;
 }
 
-// FP64 operation count of the class kernel's algorithm (an FMA counts as 2).
+// FP64 operation count of the class kernel's algorithm (an FMA counts as 2), mirroring
+// eri_kernels.cu: per primitive quartet the Gaussian-product scalars and T, per root the
+// two degree-11 Horner sums and the recurrence coefficients, the three 2D tables, and the
+// Eq. 1 products (a multiply and an FMA per [e0|f0] value and root); per contracted
+// quartet the transfer relations and the six digestion updates.
 void class_model_flops(const ClassDesc& c, int nD, int want, double* per_prim, double* per_quartet) {
   const int N = c.nroots, Le = c.Le, Lf = c.Lf;
-  double vrr = 0.0;                                   // one rys_2d call
-  if (Le >= 1) vrr += 1;
-  vrr += 4.0 * std::max(0, Le - 1);                   // fma + mul + running add
-  if (Lf >= 1) vrr += 1 + 4.0 * Le;
-  if (Lf >= 2) vrr += (Lf - 1) * (3.0 + 6.0 * Le + 1);
-  const double setup = 40.0;                          // Gaussian products, rsqrt, T, table lookup
-  const double root = 2 * 24.0 + 14.0;                // two degree-11 Horner sums + coefficients
-  *per_prim = setup + N * (root + 3 * vrr) + 3.0 * N * c.nout;
+  // scalars: s, rsqrt (4 ops), r^2, PQ (3), rz, re, T (1 + 5 + 1), locate (3), 6 scaled PQ, hs,
+  // hz*rz, he*re, Theta (2)
+  const double setup = 1 + 4 + 1 + 3 + 2 + 7 + 3 + 6 + 1 + 2 + 2;
+  const double root = 2 * 22.0 + 1 + 2 + 2 + 1 + 6 + 6;
+  double mult = 0.0, vrr = 0.0;                       // running multiples; three axes
+  if (Le >= 1) vrr += 1;                              // z: C00 * I0z
+  vrr += 3 * 3.0 * std::max(0, Le - 1);               // fma(C, I, nb10 * I)
+  mult += std::max(0, Le - 1);
+  if (Lf >= 1) {
+    vrr += 1;                                         // z: C00' * I0z
+    vrr += 3 * 3.0 * (Lf - 1);                        // row 0
+    mult += Lf - 1;
+    vrr += Le * (3 * 3.0 + 3 * 5.0 * (Lf - 1));       // rows 1..Le
+    mult += Le * (Lf - 1) + Le;
+  }
+  *per_prim = setup + N * (root + mult + vrr) + 3.0 * N * c.nout;
   double hrr = 0.0;
   for (int k = 1; k <= c.lb; ++k)
     hrr += 2.0 * (cart_below(c.la + c.lb - k + 1) - cart_below(c.la)) * ncart(k) * c.nf;
@@ -333,6 +345,7 @@ KernelArgs base_args(eri_plan* p, int X, int Y) {
   a.rys_au = p->dev->rys_au + RYS_ASYM_OFFSET[N];
   a.rys_aw = p->dev->rys_aw + RYS_ASYM_OFFSET[N];
   a.rys_tcut = RYS_TCUT[N];
+  a.rys_tcut_d = (double)RYS_TCUT[N];
   return a;
 }
 
@@ -500,6 +513,8 @@ eri_status eri_plan_create(const eri_basis* basis, const eri_opts* opts, void* c
           pp.PA[x] = pp.P[x] - A[x];
         }
         pp.E = pref / pp.zeta * std::exp(-al * be / pp.zeta * AB2) * ca * cb;
+        pp.hz = 0.5 / pp.zeta;
+        pp.pad = 0.0;
         p->prims.push_back(pp);
       }
     p->pairs_all.push_back(sp);
