@@ -60,7 +60,9 @@ typedef struct {
 typedef struct {
   double screen_thresh;      /* tau of Eqs. 6-9 (Sec. 3); shell pairs with Q <= tau are dropped */
   int precision;             /* ERI_FP64 (all FP64) or ERI_MIXED */
-  double mixed_thresh;       /* ERI_MIXED: quartets whose Schwarz x density bound is <= this run in FP32 */
+  double mixed_thresh;       /* ERI_MIXED: a quartet whose bound Q_ij Q_kl max|D| (Eqs. 7-9) is <= this
+                                runs its recurrences, Eq. 1 products, contraction and transfer in FP32;
+                                Rys roots/weights, T, digestion and J/K accumulation stay FP64 */
   int max_nd;                /* largest nD an eri_jk call may pass (>= 1) */
 } eri_opts;
 
@@ -73,7 +75,8 @@ typedef struct {
   double model_flops;             /* FP64+FP32 arithmetic of the Rys kernels, counted per class */
   int npairs_total;               /* shell pairs i >= j */
   int npairs_kept;                /* shell pairs with Q > tau */
-  int nclasses_launched;
+  int nclasses_launched;          /* class kernel launches (two per class in ERI_MIXED) */
+  double model_flops_fp32;        /* the FP32 part of model_flops (ERI_MIXED) */
 } eri_stats;
 
 /*
@@ -166,7 +169,10 @@ typedef struct {
   float ms;                       /* CUDA-event time of the launch on the call's stream */
   long long quartets;             /* shell quartets evaluated (after screening) */
   long long prim_quartets;        /* primitive quartets evaluated */
-  double model_flops;             /* FP64 arithmetic of the launch by the kernel's operation count */
+  double model_flops;             /* arithmetic of the launch by the kernel's operation count (FP64 + FP32) */
+  double model_flops_fp32;        /* its FP32 part */
+  int fp32;                       /* 1 for the FP32 path of ERI_MIXED */
+  int specialised;                /* 1 for a compile-time specialised small-class kernel */
 } eri_launch_record;
 
 /* Turn per-launch CUDA-event timing of later eri_jk calls on (1) or off (0). */

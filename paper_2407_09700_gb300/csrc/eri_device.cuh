@@ -1,0 +1,330 @@
+// Device code shared by the class kernels (eri_kernels.cu) and the compile-time
+// specialised small-class kernels (eri_small.cu).  Each translation unit gets its own
+// copy of the constant Cartesian table and uploads it at device set-up.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "eri_internal.h"
+
+#define TPB 128        // threads per block of the class kernels
+#define GSLOTS 32      // accumulator slots per lane
+
+static __constant__ unsigned char c_cart[ERI_MAXCART][4];   // lx, ly, lz, l by global Cartesian index
+
+__device__ __forceinline__ int cart_below(int l) { return l * (l + 1) * (l + 2) / 6; }
+__device__ __forceinline__ int cart_pos(int ly, int lz) { int r = ly + lz; return r * (r + 1) / 2 + lz; }
+__device__ __forceinline__ int cart_index(int lx, int ly, int lz) {
+  return cart_below(lx + ly + lz) + cart_pos(ly, lz);
+}
+
+// ------------------------------------------------------------------ shared-memory accessor
+// A team's shared region: element e lives at base[e * es].  TS = 1 interleaves the
+// 128 private regions of a block (es = 128) so that a warp reading the same entry
+// hits 32 consecutive words; larger teams use contiguous regions (es = 1).
+template <typename T>
+struct Smem {
+  T* base;
+  int es;
+  __device__ __forceinline__ T& operator[](int e) const { return base[e * es]; }
+};
+
+// ------------------------------------------------------------------ Rys roots and weights
+__device__ __forceinline__ double horner12(const double* __restrict__ c, double x) {
+  double a = __ldg(c);
+#pragma unroll
+  for (int k = 1; k <= 11; ++k) a = fma(a, x, __ldg(c + k));
+  return a;
+}
+
+// floor(T) for 0 <= T < 2^30 using integer operations only (no FP64-pipe conversion)
+__device__ __forceinline__ int floor_nonneg(double T) {
+  const long long b = __double_as_longlong(T);
+  const int e = (int)((b >> 52) & 0x7ff) - 1023;
+  if (e < 0) return 0;
+  const long long m = (b & 0xfffffffffffffLL) | 0x10000000000000LL;
+  return (int)(m >> (52 - e));
+}
+
+// Prepare the table lookup for one T: ti >= 0 selects interval ti, else the large-T limit.
+__device__ __forceinline__ void rys_locate(double T, double tcut, int& ti, double& x, double& invT, double& rsqT) {
+  if (T < tcut) {
+    ti = floor_nonneg(T);
+    x = fma(2.0, T, -(double)(2 * ti + 1));
+    invT = 0.0;
+    rsqT = 0.0;
+  } else {
+    ti = -1;
+    x = 0.0;
+    invT = 1.0 / T;
+    rsqT = rsqrt(T);
+  }
+}
+
+__device__ __forceinline__ void rys_root(const double* __restrict__ coef, const double* __restrict__ au,
+                                         const double* __restrict__ aw, int N, int ti, double x,
+                                         double invT, double rsqT, int n, double& u, double& w) {
+  if (ti >= 0) {
+    const double* c = coef + ((size_t)ti * N + n) * 24;
+    u = horner12(c, x);
+    w = horner12(c + 12, x);
+  } else {
+    u = __ldg(au + n) * invT;
+    w = __ldg(aw + n) * rsqT;
+  }
+}
+
+// ------------------------------------------------------------------ 2D recurrences
+// I(n, m) for n <= Le, m <= Lf at g[o + n*(Lf+1) + m], for the x, y and z tables at once
+// (Sec. 2's RRs in the Rys-Dupuis-King form):
+//   I(n+1, 0) = C00 I(n, 0) + n B10 I(n-1, 0)
+//   I(n, m+1) = C00' I(n, m) + n B00 I(n-1, m) + m B01 I(n, m-1)
+// I_x(0,0) = I_y(0,0) = 1 and I_z(0,0) = w Theta.  The running multiples n B10, n B00 and
+// m B01 are shared by the three axes.
+template <typename R>
+__device__ __forceinline__ void rys_2d3(const Smem<R>& g, const int o[3], int Le, int Lf, R I0z, const R C[3],
+                                        const R Cp[3], R B00, R B10, R B01) {
+  const int L1 = Lf + 1;
+  g[o[0]] = R(1);
+  g[o[1]] = R(1);
+  g[o[2]] = I0z;
+  if (Le >= 1) {
+    g[o[0] + L1] = C[0];
+    g[o[1] + L1] = C[1];
+    g[o[2] + L1] = C[2] * I0z;
+  }
+  R nb10 = B10;
+  for (int n = 1; n < Le; ++n) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      g[o[a] + (n + 1) * L1] = fma(C[a], g[o[a] + n * L1], nb10 * g[o[a] + (n - 1) * L1]);
+    nb10 += B10;
+  }
+  if (Lf == 0) return;
+  // row n = 0
+  g[o[0] + 1] = Cp[0];
+  g[o[1] + 1] = Cp[1];
+  g[o[2] + 1] = Cp[2] * I0z;
+  R mb01 = B01;
+  for (int m = 1; m < Lf; ++m) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) g[o[a] + m + 1] = fma(Cp[a], g[o[a] + m], mb01 * g[o[a] + m - 1]);
+    mb01 += B01;
+  }
+  // rows n >= 1
+  R nb00 = B00;
+  for (int n = 1; n <= Le; ++n) {
+    const int r = n * L1;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) g[o[a] + r + 1] = fma(Cp[a], g[o[a] + r], nb00 * g[o[a] + r - L1]);
+    R mb = B01;
+    for (int m = 1; m < Lf; ++m) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const int e = o[a] + r + m;
+        g[e + 1] = fma(Cp[a], g[e], fma(nb00, g[e - L1], mb * g[e - 1]));
+      }
+      mb += B01;
+    }
+    nb00 += B00;
+  }
+}
+
+// ------------------------------------------------------------------ transfer (horizontal) relations
+// Input element (e, v) at X[e*xe + v*xv] for la <= |e| <= la+lb (e relative to cart_below(la)).
+// Output contiguous [a][b][v] with |a| = la, |b| = lb; returns the output pointer (X when lb = 0).
+// Team-cooperative; every lane of the warp must call it (it contains __syncwarp).
+template <typename R>
+__device__ const R* hrr_team(int la, int lb, const double* AB, int nv, const R* X, int xe, int xv, R* bufA,
+                             R* bufB, int tl, int TS, bool active) {
+  const R ABr[3] = {(R)AB[0], (R)AB[1], (R)AB[2]};
+  const R* cur = X;
+  int cse = xe, csb = 0, csv = xv;
+  const int base = cart_below(la);
+  for (int k = 1; k <= lb; ++k) {
+    R* nxt = (cur == bufA) ? bufB : bufA;
+    const int na = cart_below(la + lb - k + 1) - base;
+    const int nb = (k + 1) * (k + 2) / 2;
+    const int total = na * nb * nv;
+    if (active) {
+      for (int t = tl; t < total; t += TS) {
+        const int v = t % nv;
+        const int r = t / nv;
+        const int ib = r % nb;
+        const int ia = r / nb;
+        const unsigned char* av = c_cart[base + ia];
+        const unsigned char* bv = c_cart[cart_below(k) + ib];
+        const int i = bv[0] ? 0 : (bv[1] ? 1 : 2);
+        int bm[3] = {bv[0], bv[1], bv[2]};
+        bm[i] -= 1;
+        const int ibm = cart_pos(bm[1], bm[2]);
+        int ap[3] = {av[0], av[1], av[2]};
+        ap[i] += 1;
+        const int iap = cart_index(ap[0], ap[1], ap[2]) - base;
+        const R hi = cur[iap * cse + ibm * csb + v * csv];
+        const R lo = cur[ia * cse + ibm * csb + v * csv];
+        nxt[(ia * nb + ib) * nv + v] = fma(ABr[i], lo, hi);
+      }
+    }
+    __syncwarp();
+    cur = nxt;
+    cse = nb * nv;
+    csb = nv;
+    csv = 1;
+  }
+  return cur;
+}
+
+// ------------------------------------------------------------------ warp helpers
+__device__ __forceinline__ int warp_max(int v) { return __reduce_max_sync(0xffffffffu, v); }
+
+// ------------------------------------------------------------------ task decoding and screening
+// Task t of a class enumerates (bra pair, ket pair): rectangular bra x ket, or the
+// triangle ket <= bra when both come from the same pair type.
+__device__ __forceinline__ void decode_task(const KernelArgs& a, long long task, int& ib, int& ik) {
+  if (a.tri) {
+    long long i = (long long)((sqrt(8.0 * (double)task + 1.0) - 1.0) * 0.5);
+    while (i * (i + 1) / 2 > task) --i;
+    while ((i + 1) * (i + 2) / 2 <= task) ++i;
+    ib = a.bra0 + (int)i;
+    ik = a.ket0 + (int)(task - i * (i + 1) / 2);
+  } else {
+    ib = a.bra0 + (int)(task / a.nket);
+    ik = a.ket0 + (int)(task % a.nket);
+  }
+}
+
+// Q_ij Q_kl max|D| over the six cross blocks (Eqs. 7-9)
+__device__ __forceinline__ double quartet_bound(const KernelArgs& a, const ShellPair* bra, const ShellPair* ket) {
+  const int P = bra->sh0, Qs = bra->sh1, Rr = ket->sh0, S = ket->sh1;
+  const double* Dm = a.Dmax;
+  const int n = a.nsh;
+  const double dm = fmax(fmax(Dm[P * n + Qs], Dm[Rr * n + S]),
+                         fmax(fmax(Dm[P * n + Rr], Dm[P * n + S]), fmax(Dm[Qs * n + Rr], Dm[Qs * n + S])));
+  return bra->Q * ket->Q * dm;
+}
+
+// Per-primitive-quartet scalars in shared memory: NPD doubles (root lookup, FP64 always)
+// followed by NPR values of the recurrence type R.
+#define NPD 4
+#define NPR 18
+
+template <typename R> struct PairOf;
+template <> struct PairOf<double> { typedef PrimPair type; };
+template <> struct PairOf<float> { typedef PrimPairF type; };
+
+__device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
+__device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
+
+// Transfer relations on the contracted [e0|f0] in E0, then digestion into J~ / K~ (KMODE_JK),
+// the block (KMODE_BLOCK) or the diagonal maximum (KMODE_SCHWARZ).  Team-cooperative;
+// every lane of the warp calls it.
+template <int TS, typename R>
+__device__ __forceinline__ void finish_quartet(const KernelArgs& a, const ClassDesc& c, R* E0, R* bufA, R* bufB,
+                                               int tl, bool active, const double* AB, const double* CD,
+                                               const ShellPair* bra, const ShellPair* ket, int ib, int ik,
+                                               long long task) {
+  // ---- 2. transfer relations: bra on e (vector over f), then ket on f (vector over ab)
+  const int nab = c.na * c.nb, ncd = c.nc * c.nd;
+  const R* Y = hrr_team<R>(c.la, c.lb, AB, c.nf, E0, c.nf, 1, bufA, bufB, tl, TS, active);
+  const R* G = hrr_team<R>(c.lc, c.ld, CD, nab, Y, 1, c.nf, bufA, bufB, tl, TS, active);
+  // (ab|cd) = G[ab*sab + cd*scd]
+  const int sab = (c.ld > 0) ? 1 : c.nf;
+  const int scd = (c.ld > 0) ? nab : 1;
+
+  // ---- 3. digestion (FP64) / output
+  if (a.mode == KMODE_JK) {
+    if (active) {
+      double w = 1.0;
+      if (bra->sh0 == bra->sh1) w *= 0.5;
+      if (ket->sh0 == ket->sh1) w *= 0.5;
+      if (ib == ik) w *= 0.5;
+      const int p0 = bra->bf0, q0b = bra->bf1, r0 = ket->bf0, s0 = ket->bf1;
+      const int na = c.na, nb = c.nb, nc = c.nc, nd = c.nd;
+      const int nbf = a.nbf;
+      for (int xd = 0; xd < a.nD; ++xd) {
+        const double* Dx = a.D + (size_t)xd * nbf * nbf;
+        if (a.want & 1) {
+          double* Jx = a.J + (size_t)xd * nbf * nbf;
+          for (int t = tl; t < nab; t += TS) {
+            const int ia = t / nb, ibb = t - (t / nb) * nb;
+            double s = 0.0;
+            for (int cd = 0; cd < ncd; ++cd) {
+              const int ic = cd / nd, id = cd - (cd / nd) * nd;
+              s = fma((double)G[t * sab + cd * scd], __ldg(Dx + (size_t)(r0 + ic) * nbf + s0 + id), s);
+            }
+            atomicAdd(Jx + (size_t)(p0 + ia) * nbf + q0b + ibb, 2.0 * w * s);
+          }
+          for (int t = tl; t < ncd; t += TS) {
+            const int ic = t / nd, id = t - (t / nd) * nd;
+            double s = 0.0;
+            for (int ab = 0; ab < nab; ++ab) {
+              const int ia = ab / nb, ibb = ab - (ab / nb) * nb;
+              s = fma((double)G[ab * sab + t * scd], __ldg(Dx + (size_t)(p0 + ia) * nbf + q0b + ibb), s);
+            }
+            atomicAdd(Jx + (size_t)(r0 + ic) * nbf + s0 + id, 2.0 * w * s);
+          }
+        }
+        if (a.want & 2) {
+          double* Kx = a.K + (size_t)xd * nbf * nbf;
+          // K_ac += w sum_bd g D_bd
+          for (int t = tl; t < na * nc; t += TS) {
+            const int ia = t / nc, ic = t - (t / nc) * nc;
+            double s = 0.0;
+            for (int ibb = 0; ibb < nb; ++ibb)
+              for (int id = 0; id < nd; ++id)
+                s = fma((double)G[(ia * nb + ibb) * sab + (ic * nd + id) * scd],
+                        __ldg(Dx + (size_t)(q0b + ibb) * nbf + s0 + id), s);
+            atomicAdd(Kx + (size_t)(p0 + ia) * nbf + r0 + ic, w * s);
+          }
+          // K_bd += w sum_ac g D_ac
+          for (int t = tl; t < nb * nd; t += TS) {
+            const int ibb = t / nd, id = t - (t / nd) * nd;
+            double s = 0.0;
+            for (int ia = 0; ia < na; ++ia)
+              for (int ic = 0; ic < nc; ++ic)
+                s = fma((double)G[(ia * nb + ibb) * sab + (ic * nd + id) * scd],
+                        __ldg(Dx + (size_t)(p0 + ia) * nbf + r0 + ic), s);
+            atomicAdd(Kx + (size_t)(q0b + ibb) * nbf + s0 + id, w * s);
+          }
+          // K_ad += w sum_bc g D_bc
+          for (int t = tl; t < na * nd; t += TS) {
+            const int ia = t / nd, id = t - (t / nd) * nd;
+            double s = 0.0;
+            for (int ibb = 0; ibb < nb; ++ibb)
+              for (int ic = 0; ic < nc; ++ic)
+                s = fma((double)G[(ia * nb + ibb) * sab + (ic * nd + id) * scd],
+                        __ldg(Dx + (size_t)(q0b + ibb) * nbf + r0 + ic), s);
+            atomicAdd(Kx + (size_t)(p0 + ia) * nbf + s0 + id, w * s);
+          }
+          // K_bc += w sum_ad g D_ad
+          for (int t = tl; t < nb * nc; t += TS) {
+            const int ibb = t / nc, ic = t - (t / nc) * nc;
+            double s = 0.0;
+            for (int ia = 0; ia < na; ++ia)
+              for (int id = 0; id < nd; ++id)
+                s = fma((double)G[(ia * nb + ibb) * sab + (ic * nd + id) * scd],
+                        __ldg(Dx + (size_t)(p0 + ia) * nbf + s0 + id), s);
+            atomicAdd(Kx + (size_t)(q0b + ibb) * nbf + r0 + ic, w * s);
+          }
+        }
+      }
+    }
+  } else if (a.mode == KMODE_BLOCK) {
+    if (active) {
+      double* out = a.blockout + a.blockoff[task];
+      for (int t = tl; t < nab * ncd; t += TS) {
+        const int ab = t / ncd, cd = t - (t / ncd) * ncd;
+        out[t] = (double)G[ab * sab + cd * scd];
+      }
+    }
+  } else {  // KMODE_SCHWARZ: bra and ket are the same pair; max_{a,b} |(ab|ab)|
+    double m = 0.0;
+    if (active)
+      for (int t = tl; t < nab; t += TS) m = fmax(m, fabs((double)G[t * sab + t * scd]));
+    if (TS > 1) {
+      for (int off = TS / 2; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
+    }
+    if (active && tl == 0) a.qout[task] = m;
+  }
+}

@@ -18,6 +18,16 @@ struct PrimPair {
   double pad;
 };
 
+// FP32 shadow of PrimPair for the FP32 path of the mixed mode.  40 bytes.
+struct PrimPairF {
+  float zeta;
+  float P[3];
+  float PA[3];
+  float E;
+  float hz;
+  float pad;
+};
+
 // One shell pair in canonical orientation (l of sh0 >= l of sh1).  64 bytes.
 struct ShellPair {
   int sh0, sh1;    // shell indices
@@ -42,7 +52,8 @@ struct ClassDesc {
   int e_base, f_base;    // global Cartesian index of the first e / f
   int npass;             // output chunks of TS*G values
   int bp;                // primitive quartets per batch (team kernels)
-  int team_doubles;      // shared-memory doubles per team
+  int team_doubles;      // shared-memory doubles per team (FP64 recurrences)
+  int team_doubles_f32;  // shared-memory doubles per team (FP32 recurrences)
   int hrr_doubles;       // size of one HRR ping-pong buffer (doubles)
   long long scratch_per_team;  // global scratch doubles per team
   const uint32_t* outidx;      // [nout] packed 2D offsets ix | iy << 8 | iz << 16
@@ -54,6 +65,7 @@ struct KernelArgs {
   ClassDesc c;
   const ShellPair* pairs;
   const PrimPair* prims;
+  const PrimPairF* primsf;     // FP32 shadow (FP32 kernels)
   // task space: bra pairs [bra0, bra0+nbra), ket pairs [ket0, ket0+nket); tri = same range, ket <= bra
   int bra0, nbra, ket0, nket, tri;
   long long ntask;
@@ -61,6 +73,14 @@ struct KernelArgs {
   const double* Dmax;    // [nsh][nsh]
   int nsh;
   double tau;
+  int prec_sel;          // 0: every kept quartet; 1: bound > mixed_thr only; 2: bound <= mixed_thr only
+  double mixed_thr;
+  // compacted task lists (KMODE_JK): when tlist is set, the tasks are tlist[0 .. *tcount) or,
+  // with from_back, tlist[cap-1-t] for t < *tcount; they already passed the screen
+  const unsigned* tlist;
+  const unsigned long long* tcount;
+  unsigned long long list_cap;
+  int from_back;
   // densities and outputs (KMODE_JK): row-major [nD][nbf][nbf]
   const double* D;
   double* J;
@@ -90,14 +110,21 @@ extern "C" {
 #endif
 int erik_upload_cart_tables(void);
 int erik_team_config(int ts, int* threads_per_block, int* max_g);
-int erik_blocks_per_sm(int ts, int smem_bytes, int* out);
-int erik_launch_class(int ts, const struct KernelArgs* a, int grid, int smem_bytes, void* stream);
+int erik_blocks_per_sm(int ts, int fp32, int smem_bytes, int* out);
+int erik_launch_class(int ts, int fp32, const struct KernelArgs* a, int grid, int smem_bytes, void* stream);
+int erik_launch_compact(const struct KernelArgs* a, unsigned* tlist, unsigned long long cap,
+                        unsigned long long* counts, unsigned* tiles, int mixed, void* stream);
 int erik_launch_dmax(const double* D, int nD, int nbf, int nsh, const int* sh_bf0, const int* sh_n,
                      double* Dmax, void* stream);
 int erik_launch_symmetrize(double* M, int nD, int nbf, void* stream);
 int erik_launch_rys(int N, int n, const double* T, double* u, double* w, const double* coef,
                     const double* au, const double* aw, int tcut, void* stream);
 int erik_probe_fma(double* fp64_tflops, double* fp32_tflops);
+// compile-time specialised kernels of the small classes (eri_small.cu)
+int erik_upload_cart_tables_small(void);
+int erik_small_available(int la, int lb, int lc, int ld);
+int erik_small_blocks_per_sm(int la, int lb, int lc, int ld, int fp32, int* out);
+int erik_launch_small(int la, int lb, int lc, int ld, int fp32, const struct KernelArgs* a, int grid, void* stream);
 #ifdef __cplusplus
 }
 #endif

@@ -24,179 +24,123 @@
 
 #include "eri_internal.h"
 
-#define TPB 128        // threads per block of the class kernels
-#define GSLOTS 32      // accumulator slots per lane
-#define NPS 24         // shared doubles of per-primitive-quartet scalars
+#include "eri_device.cuh"
 
-__constant__ unsigned char c_cart[ERI_MAXCART][4];   // lx, ly, lz, l by global Cartesian index
-
-__device__ __forceinline__ int cart_below(int l) { return l * (l + 1) * (l + 2) / 6; }
-__device__ __forceinline__ int cart_pos(int ly, int lz) { int r = ly + lz; return r * (r + 1) / 2 + lz; }
-__device__ __forceinline__ int cart_index(int lx, int ly, int lz) {
-  return cart_below(lx + ly + lz) + cart_pos(ly, lz);
+// Stable compaction of a class's task space into the FP64 list (front of tlist, ascending
+// task order) and, in the mixed mode, the FP32 list (back of tlist, read back-to-front in
+// ascending task order).  Three steps: per-tile counts, an exclusive scan over tiles,
+// ordered writes.  Keeping the order keeps neighbouring tasks on the same bra pair and on
+// ket pairs of equal contraction depth, so a warp's primitive loops stay uniform.
+#define CTILE 1024
+__device__ __forceinline__ int task_category(const KernelArgs& a, long long task, int mixed) {
+  if (task >= a.ntask) return 0;
+  int ib, ik;
+  decode_task(a, task, ib, ik);
+  const double bound = quartet_bound(a, a.pairs + ib, a.pairs + ik);
+  if (!(bound >= a.tau)) return 0;
+  return (mixed && !(bound > a.mixed_thr)) ? 2 : 1;
 }
 
-// ------------------------------------------------------------------ shared-memory accessor
-// A team's shared region: element e lives at base[e * es].  TS = 1 interleaves the
-// 128 private regions of a block (es = 128) so that a warp reading the same entry
-// hits 32 consecutive words; larger teams use contiguous regions (es = 1).
-struct Smem {
-  double* base;
-  int es;
-  __device__ __forceinline__ double& operator[](int e) const { return base[e * es]; }
-};
-
-// ------------------------------------------------------------------ Rys roots and weights
-__device__ __forceinline__ double horner12(const double* __restrict__ c, double x) {
-  double a = __ldg(c);
-#pragma unroll
-  for (int k = 1; k <= 11; ++k) a = fma(a, x, __ldg(c + k));
-  return a;
-}
-
-// floor(T) for 0 <= T < 2^30 using integer operations only (no FP64-pipe conversion)
-__device__ __forceinline__ int floor_nonneg(double T) {
-  const long long b = __double_as_longlong(T);
-  const int e = (int)((b >> 52) & 0x7ff) - 1023;
-  if (e < 0) return 0;
-  const long long m = (b & 0xfffffffffffffLL) | 0x10000000000000LL;
-  return (int)(m >> (52 - e));
-}
-
-// Prepare the table lookup for one T: ti >= 0 selects interval ti, else the large-T limit.
-__device__ __forceinline__ void rys_locate(double T, double tcut, int& ti, double& x, double& invT, double& rsqT) {
-  if (T < tcut) {
-    ti = floor_nonneg(T);
-    x = fma(2.0, T, -(double)(2 * ti + 1));
-    invT = 0.0;
-    rsqT = 0.0;
-  } else {
-    ti = -1;
-    x = 0.0;
-    invT = 1.0 / T;
-    rsqT = rsqrt(T);
+// Block-wide counts of categories 1 and 2 over one tile (256 threads x 4 tasks).
+__global__ void compact_count_kernel(const KernelArgs a, int mixed, unsigned* tilecnt) {
+  __shared__ unsigned s1[8], s2[8];
+  const long long t0 = (long long)blockIdx.x * CTILE;
+  unsigned c1 = 0, c2 = 0;
+  for (int k = 0; k < CTILE / 256; ++k) {
+    const int cat = task_category(a, t0 + k * 256 + threadIdx.x, mixed);
+    c1 += cat == 1;
+    c2 += cat == 2;
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    c1 += __shfl_xor_sync(0xffffffffu, c1, off);
+    c2 += __shfl_xor_sync(0xffffffffu, c2, off);
+  }
+  if ((threadIdx.x & 31) == 0) { s1[threadIdx.x >> 5] = c1; s2[threadIdx.x >> 5] = c2; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned t1 = 0, t2 = 0;
+    for (int w = 0; w < 8; ++w) { t1 += s1[w]; t2 += s2[w]; }
+    tilecnt[2 * blockIdx.x] = t1;
+    tilecnt[2 * blockIdx.x + 1] = t2;
   }
 }
 
-__device__ __forceinline__ void rys_root(const double* __restrict__ coef, const double* __restrict__ au,
-                                         const double* __restrict__ aw, int N, int ti, double x,
-                                         double invT, double rsqT, int n, double& u, double& w) {
-  if (ti >= 0) {
-    const double* c = coef + ((size_t)ti * N + n) * 24;
-    u = horner12(c, x);
-    w = horner12(c + 12, x);
-  } else {
-    u = __ldg(au + n) * invT;
-    w = __ldg(aw + n) * rsqT;
-  }
-}
-
-// ------------------------------------------------------------------ 2D recurrences
-// I(n, m) for n <= Le, m <= Lf at g[o + n*(Lf+1) + m], for the x, y and z tables at once
-// (Sec. 2's RRs in the Rys-Dupuis-King form):
-//   I(n+1, 0) = C00 I(n, 0) + n B10 I(n-1, 0)
-//   I(n, m+1) = C00' I(n, m) + n B00 I(n-1, m) + m B01 I(n, m-1)
-// I_x(0,0) = I_y(0,0) = 1 and I_z(0,0) = w Theta.  The running multiples n B10, n B00 and
-// m B01 are shared by the three axes.
-__device__ __forceinline__ void rys_2d3(const Smem& g, const int o[3], int Le, int Lf, double I0z,
-                                        const double C[3], const double Cp[3], double B00, double B10,
-                                        double B01) {
-  const int L1 = Lf + 1;
-  g[o[0]] = 1.0;
-  g[o[1]] = 1.0;
-  g[o[2]] = I0z;
-  if (Le >= 1) {
-    g[o[0] + L1] = C[0];
-    g[o[1] + L1] = C[1];
-    g[o[2] + L1] = C[2] * I0z;
-  }
-  double nb10 = B10;
-  for (int n = 1; n < Le; ++n) {
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-      g[o[a] + (n + 1) * L1] = fma(C[a], g[o[a] + n * L1], nb10 * g[o[a] + (n - 1) * L1]);
-    nb10 += B10;
-  }
-  if (Lf == 0) return;
-  // row n = 0
-  g[o[0] + 1] = Cp[0];
-  g[o[1] + 1] = Cp[1];
-  g[o[2] + 1] = Cp[2] * I0z;
-  double mb01 = B01;
-  for (int m = 1; m < Lf; ++m) {
-#pragma unroll
-    for (int a = 0; a < 3; ++a) g[o[a] + m + 1] = fma(Cp[a], g[o[a] + m], mb01 * g[o[a] + m - 1]);
-    mb01 += B01;
-  }
-  // rows n >= 1
-  double nb00 = B00;
-  for (int n = 1; n <= Le; ++n) {
-    const int r = n * L1;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) g[o[a] + r + 1] = fma(Cp[a], g[o[a] + r], nb00 * g[o[a] + r - L1]);
-    double mb = B01;
-    for (int m = 1; m < Lf; ++m) {
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        const int e = o[a] + r + m;
-        g[e + 1] = fma(Cp[a], g[e], fma(nb00, g[e - L1], mb * g[e - 1]));
-      }
-      mb += B01;
+// Exclusive scan of the tile counts (one block); totals to counts[0..1].
+__global__ void compact_scan_kernel(unsigned* tilecnt, long long ntiles, unsigned long long* counts) {
+  __shared__ unsigned long long w1[32], w2[32];
+  __shared__ unsigned long long carry1, carry2;
+  if (threadIdx.x == 0) { carry1 = 0; carry2 = 0; }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (long long base = 0; base < ntiles; base += blockDim.x) {
+    const long long i = base + threadIdx.x;
+    unsigned long long v1 = (i < ntiles) ? tilecnt[2 * i] : 0, v2 = (i < ntiles) ? tilecnt[2 * i + 1] : 0;
+    unsigned long long x1 = v1, x2 = v2;
+    for (int off = 1; off < 32; off <<= 1) {
+      const unsigned long long y1 = __shfl_up_sync(0xffffffffu, x1, off);
+      const unsigned long long y2 = __shfl_up_sync(0xffffffffu, x2, off);
+      if (lane >= off) { x1 += y1; x2 += y2; }
     }
-    nb00 += B00;
-  }
-}
-
-// ------------------------------------------------------------------ transfer (horizontal) relations
-// Input element (e, v) at X[e*xe + v*xv] for la <= |e| <= la+lb (e relative to cart_below(la)).
-// Output contiguous [a][b][v] with |a| = la, |b| = lb; returns the output pointer (X when lb = 0).
-// Team-cooperative; every lane of the warp must call it (it contains __syncwarp).
-__device__ const double* hrr_team(int la, int lb, const double* AB, int nv, const double* X, int xe,
-                                  int xv, double* bufA, double* bufB, int tl, int TS, bool active) {
-  const double* cur = X;
-  int cse = xe, csb = 0, csv = xv;
-  const int base = cart_below(la);
-  for (int k = 1; k <= lb; ++k) {
-    double* nxt = (cur == bufA) ? bufB : bufA;
-    const int na = cart_below(la + lb - k + 1) - base;
-    const int nb = (k + 1) * (k + 2) / 2;
-    const int total = na * nb * nv;
-    if (active) {
-      for (int t = tl; t < total; t += TS) {
-        const int v = t % nv;
-        const int r = t / nv;
-        const int ib = r % nb;
-        const int ia = r / nb;
-        const unsigned char* av = c_cart[base + ia];
-        const unsigned char* bv = c_cart[cart_below(k) + ib];
-        const int i = bv[0] ? 0 : (bv[1] ? 1 : 2);
-        int bm[3] = {bv[0], bv[1], bv[2]};
-        bm[i] -= 1;
-        const int ibm = cart_pos(bm[1], bm[2]);
-        int ap[3] = {av[0], av[1], av[2]};
-        ap[i] += 1;
-        const int iap = cart_index(ap[0], ap[1], ap[2]) - base;
-        const double hi = cur[iap * cse + ibm * csb + v * csv];
-        const double lo = cur[ia * cse + ibm * csb + v * csv];
-        nxt[(ia * nb + ib) * nv + v] = fma(AB[i], lo, hi);
+    if (lane == 31) { w1[wid] = x1; w2[wid] = x2; }
+    __syncthreads();
+    if (wid == 0) {
+      const int nw = blockDim.x >> 5;
+      unsigned long long z1 = (lane < nw) ? w1[lane] : 0, z2 = (lane < nw) ? w2[lane] : 0;
+      for (int off = 1; off < 32; off <<= 1) {
+        const unsigned long long y1 = __shfl_up_sync(0xffffffffu, z1, off);
+        const unsigned long long y2 = __shfl_up_sync(0xffffffffu, z2, off);
+        if (lane >= off) { z1 += y1; z2 += y2; }
       }
+      if (lane < nw) { w1[lane] = z1; w2[lane] = z2; }
     }
-    __syncwarp();
-    cur = nxt;
-    cse = nb * nv;
-    csb = nv;
-    csv = 1;
+    __syncthreads();
+    const unsigned long long pre1 = carry1 + (wid ? w1[wid - 1] : 0) + x1 - v1;
+    const unsigned long long pre2 = carry2 + (wid ? w2[wid - 1] : 0) + x2 - v2;
+    __syncthreads();
+    if (i < ntiles) { tilecnt[2 * i] = (unsigned)pre1; tilecnt[2 * i + 1] = (unsigned)pre2; }
+    if (threadIdx.x == blockDim.x - 1) { carry1 = pre1 + v1; carry2 = pre2 + v2; }
+    __syncthreads();
   }
-  return cur;
+  if (threadIdx.x == 0) { counts[0] = carry1; counts[1] = carry2; }
 }
 
-// ------------------------------------------------------------------ warp helpers
-__device__ __forceinline__ int warp_max(int v) { return __reduce_max_sync(0xffffffffu, v); }
+// Ordered writes: each tile recomputes its categories and writes at its scanned offset.
+__global__ void compact_write_kernel(const KernelArgs a, int mixed, const unsigned* tileoff, unsigned* tlist,
+                                     unsigned long long cap) {
+  __shared__ unsigned s1[8], s2[8];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const long long t0 = (long long)blockIdx.x * CTILE;
+  unsigned base1 = tileoff[2 * blockIdx.x], base2 = tileoff[2 * blockIdx.x + 1];
+  for (int k = 0; k < CTILE / 256; ++k) {
+    const long long task = t0 + k * 256 + threadIdx.x;
+    const int cat = task_category(a, task, mixed);
+    const unsigned m1 = __ballot_sync(0xffffffffu, cat == 1), m2 = __ballot_sync(0xffffffffu, cat == 2);
+    if (lane == 0) { s1[wid] = __popc(m1); s2[wid] = __popc(m2); }
+    __syncthreads();
+    unsigned p1 = base1, p2 = base2, tot1 = 0, tot2 = 0;
+    for (int w = 0; w < 8; ++w) {
+      if (w < wid) { p1 += s1[w]; p2 += s2[w]; }
+      tot1 += s1[w];
+      tot2 += s2[w];
+    }
+    const unsigned below = (1u << lane) - 1u;
+    if (cat == 1) tlist[p1 + __popc(m1 & below)] = (unsigned)task;
+    if (cat == 2) tlist[cap - 1 - (p2 + __popc(m2 & below))] = (unsigned)task;
+    base1 += tot1;
+    base2 += tot2;
+    __syncthreads();
+  }
+}
 
 // ------------------------------------------------------------------ the class kernel
-template <int TS>
-__global__ void __launch_bounds__(TPB) eri_class_kernel(const KernelArgs a) {
+// R = double: the FP64 path.  R = float: the FP32 path of the mixed mode (Sec. 2's
+// recurrences, Eq. 1's products, the Eq. 5 contraction and the transfer relations in
+// FP32; T and the Rys roots / weights in FP64, rounded at the recurrence input;
+// digestion and the J / K accumulation in FP64).
+template <int TS, typename R>
+__global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : 2)) eri_class_kernel(const KernelArgs a) {
   extern __shared__ double smem[];
+  typedef typename PairOf<R>::type PP;
   constexpr int TEAMS_PER_WARP = 32 / TS;
   const int lane = threadIdx.x & 31;
   const int tl = lane % TS;                          // lane within team
@@ -206,33 +150,40 @@ __global__ void __launch_bounds__(TPB) eri_class_kernel(const KernelArgs a) {
   const int N = c.nroots, nI = c.nI, Le = c.Le, Lf = c.Lf;
   const int bp = c.bp;
 
-  Smem sm;
+  // team region: [bp][NPD] doubles, then [bp][NPR] R, then [bp][3][N][nI] R
+  Smem<double> sd;
+  Smem<R> sr;
   if (TS == 1) {
-    sm.base = smem + threadIdx.x;
-    sm.es = TPB;
+    sd.base = smem + threadIdx.x;
+    sd.es = TPB;
+    sr.base = reinterpret_cast<R*>(smem + (size_t)TPB * bp * NPD) + threadIdx.x;
+    sr.es = TPB;
   } else {
-    sm.base = smem + (size_t)team_in_block * c.team_doubles;
-    sm.es = 1;
+    sd.base = smem + (size_t)team_in_block * (sizeof(R) == 8 ? c.team_doubles : c.team_doubles_f32);
+    sd.es = 1;
+    sr.base = reinterpret_cast<R*>(sd.base + bp * NPD);
+    sr.es = 1;
   }
-  double* scr = a.scratch + gteam * c.scratch_per_team;
-  double* E0 = scr;                                  // [ne][nf] contracted [e0|f0]
-  double* bufA = scr + c.nout;
-  double* bufB = bufA + c.hrr_doubles;
-
-  // layout of the shared team region
-  const int S_PRIM = 0;                              // [bp][NPS]
-  const int S_2D = bp * NPS;                         // [bp][3][N][nI]
+  const int S_2D = bp * NPR;                         // R offset of the 2D tables
+  R* scr = reinterpret_cast<R*>(a.scratch + gteam * c.scratch_per_team);
+  R* E0 = scr;                                       // [ne][nf] contracted [e0|f0]
+  R* bufA = scr + c.nout;
+  R* bufB = bufA + c.hrr_doubles;
+  const PP* prims_r = reinterpret_cast<const PP*>(sizeof(R) == 8 ? (const void*)a.prims : (const void*)a.primsf);
 
   unsigned long long cnt_q = 0, cnt_p = 0;
+
+  const bool listed = (a.mode == KMODE_JK) && (a.tlist != nullptr);
+  const long long ntask = listed ? (long long)*a.tcount : a.ntask;
 
   while (true) {
     // ---- fetch TEAMS_PER_WARP tasks per warp
     unsigned long long tbase = 0;
     if (lane == 0) tbase = atomicAdd(a.counter, (unsigned long long)TEAMS_PER_WARP);
     tbase = __shfl_sync(0xffffffffu, tbase, 0);
-    if (tbase >= (unsigned long long)a.ntask) break;
+    if (tbase >= (unsigned long long)ntask) break;
     const long long task = (long long)tbase + lane / TS;
-    bool active = task < a.ntask;
+    bool active = task < ntask;
 
     // ---- decode the task into (bra pair, ket pair)
     int ib = 0, ik = 0;
@@ -240,27 +191,23 @@ __global__ void __launch_bounds__(TPB) eri_class_kernel(const KernelArgs a) {
       if (a.mode != KMODE_JK) {
         ib = a.tasklist[2 * task];
         ik = a.tasklist[2 * task + 1];
-      } else if (a.tri) {
-        long long i = (long long)((sqrt(8.0 * (double)task + 1.0) - 1.0) * 0.5);
-        while (i * (i + 1) / 2 > task) --i;
-        while ((i + 1) * (i + 2) / 2 <= task) ++i;
-        ib = a.bra0 + (int)i;
-        ik = a.ket0 + (int)(task - i * (i + 1) / 2);
+      } else if (listed) {
+        const unsigned t = a.from_back ? a.tlist[a.list_cap - 1 - (unsigned long long)task] : a.tlist[task];
+        decode_task(a, (long long)t, ib, ik);
       } else {
-        ib = a.bra0 + (int)(task / a.nket);
-        ik = a.ket0 + (int)(task % a.nket);
+        decode_task(a, task, ib, ik);
       }
     }
     const ShellPair* bra = a.pairs + ib;
     const ShellPair* ket = a.pairs + ik;
-    // ---- screening (Eqs. 7-9): Q_ij Q_kl max|D| over the six cross blocks >= tau
-    if (active && a.mode == KMODE_JK) {
-      const int P = bra->sh0, Qs = bra->sh1, R = ket->sh0, S = ket->sh1;
-      const double* Dm = a.Dmax;
-      const int n = a.nsh;
-      double dm = fmax(fmax(Dm[P * n + Qs], Dm[R * n + S]),
-                       fmax(fmax(Dm[P * n + R], Dm[P * n + S]), fmax(Dm[Qs * n + R], Dm[Qs * n + S])));
-      active = bra->Q * ket->Q * dm >= a.tau;
+    // ---- screening (Eqs. 7-9): Q_ij Q_kl max|D| over the six cross blocks >= tau;
+    //      in the mixed mode the same bound picks the precision (FP64 above mixed_thr).
+    //      Listed tasks were screened by compact_kernel.
+    if (active && a.mode == KMODE_JK && !listed) {
+      const double bound = quartet_bound(a, bra, ket);
+      active = bound >= a.tau;
+      if (a.prec_sel == 1) active = active && bound > a.mixed_thr;
+      if (a.prec_sel == 2) active = active && !(bound > a.mixed_thr);
     }
     const int npb = active ? bra->nprim : 0;
     const int npk = active ? ket->nprim : 0;
@@ -273,78 +220,91 @@ __global__ void __launch_bounds__(TPB) eri_class_kernel(const KernelArgs a) {
       AB[0] = bra->AB[0]; AB[1] = bra->AB[1]; AB[2] = bra->AB[2];
       CD[0] = ket->AB[0]; CD[1] = ket->AB[1]; CD[2] = ket->AB[2];
     }
-    const PrimPair* pb = a.prims + (active ? bra->prim_off : 0);
-    const PrimPair* pk = a.prims + (active ? ket->prim_off : 0);
+    const int boff = active ? bra->prim_off : 0, koff = active ? ket->prim_off : 0;
 
     for (int pass = 0; pass < c.npass; ++pass) {
       // ---- my output slots for this pass
       const int o0 = pass * TS * GSLOTS;
       uint32_t pkd[GSLOTS];
-      double acc[GSLOTS];
+      R acc[GSLOTS];
 #pragma unroll
       for (int k = 0; k < GSLOTS; ++k) {
         const int o = o0 + k * TS + tl;
-        pkd[k] = (o < c.nout) ? __ldg(c.outidx + o) : 0u;
-        acc[k] = 0.0;
+        // TS = 1: every lane has the same slots, so the index is re-read (broadcast) instead
+        if (TS > 1) pkd[k] = (o < c.nout) ? __ldg(c.outidx + o) : 0u;
+        acc[k] = R(0);
       }
       const int kcnt = min(GSLOTS, (c.nout - o0 + TS - 1) / TS);   // uniform
 
       for (int q0 = 0; q0 < maxq; q0 += bp) {
         const int nbt = min(bp, nq - q0);            // this team's primitives in the batch (may be <= 0)
-        // ---- a. primitive-quartet scalars
+        // ---- a. primitive-quartet scalars: T and the table lookup in FP64, the rest in R
         for (int j = tl; j < bp; j += TS) {
           if (j < nbt) {
             const int q = q0 + j;
-            const PrimPair* x = pb + q / npk;
-            const PrimPair* y = pk + q % npk;
-            const double zeta = x->zeta, eta = y->zeta;
-            const double s = zeta + eta;
-            const double r = rsqrt(s);
-            const double inv_s = r * r;
-            const double PQ0 = x->P[0] - y->P[0], PQ1 = x->P[1] - y->P[1], PQ2 = x->P[2] - y->P[2];
-            const double rz = eta * inv_s, re = zeta * inv_s;
-            const double T = zeta * rz * fma(PQ0, PQ0, fma(PQ1, PQ1, PQ2 * PQ2));
+            const int ixp = boff + q / npk, iyp = koff + q % npk;
+            const PrimPair* xd = a.prims + ixp;
+            const PrimPair* yd = a.prims + iyp;
+            const double s = xd->zeta + yd->zeta;
+            const double rd = rsqrt(s);
+            const double PQ0 = xd->P[0] - yd->P[0], PQ1 = xd->P[1] - yd->P[1], PQ2 = xd->P[2] - yd->P[2];
+            const double T = xd->zeta * yd->zeta * (rd * rd) * fma(PQ0, PQ0, fma(PQ1, PQ1, PQ2 * PQ2));
             int ti;
             double xx, invT, rsqT;
             rys_locate(T, a.rys_tcut_d, ti, xx, invT, rsqT);
-            const double hz = x->hz, he = y->hz;
-            const int o = S_PRIM + j * NPS;
-            sm[o + 0] = x->PA[0]; sm[o + 1] = x->PA[1]; sm[o + 2] = x->PA[2];
-            sm[o + 3] = y->PA[0]; sm[o + 4] = y->PA[1]; sm[o + 5] = y->PA[2];
-            sm[o + 6] = rz * PQ0; sm[o + 7] = rz * PQ1; sm[o + 8] = rz * PQ2;
-            sm[o + 9] = re * PQ0; sm[o + 10] = re * PQ1; sm[o + 11] = re * PQ2;
-            sm[o + 12] = 0.5 * inv_s;
-            sm[o + 13] = hz;
-            sm[o + 14] = he;
-            sm[o + 15] = hz * rz;
-            sm[o + 16] = he * re;
-            sm[o + 17] = x->E * y->E * r;           // Theta with contraction coefficients
-            sm[o + 18] = xx;
-            sm[o + 19] = invT;
-            sm[o + 20] = rsqT;
-            sm[o + 21] = __longlong_as_double((long long)ti);
+            const int od = j * NPD;
+            sd[od + 0] = xx;
+            sd[od + 1] = invT;
+            sd[od + 2] = rsqT;
+            sd[od + 3] = __longlong_as_double((long long)ti);
+            const PP* x = (sizeof(R) == 8) ? reinterpret_cast<const PP*>(xd) : prims_r + ixp;
+            const PP* y = (sizeof(R) == 8) ? reinterpret_cast<const PP*>(yd) : prims_r + iyp;
+            const R zeta = x->zeta, eta = y->zeta;
+            R r, inv_s, P0, P1, P2;
+            if (sizeof(R) == 8) {
+              r = (R)rd;
+              P0 = (R)PQ0; P1 = (R)PQ1; P2 = (R)PQ2;
+            } else {
+              r = rsqrt_t(zeta + eta);
+              P0 = x->P[0] - y->P[0]; P1 = x->P[1] - y->P[1]; P2 = x->P[2] - y->P[2];
+            }
+            inv_s = r * r;
+            const R rz = eta * inv_s, re = zeta * inv_s;
+            const R hz = x->hz, he = y->hz;
+            const int o = j * NPR;
+            sr[o + 0] = x->PA[0]; sr[o + 1] = x->PA[1]; sr[o + 2] = x->PA[2];
+            sr[o + 3] = y->PA[0]; sr[o + 4] = y->PA[1]; sr[o + 5] = y->PA[2];
+            sr[o + 6] = rz * P0; sr[o + 7] = rz * P1; sr[o + 8] = rz * P2;
+            sr[o + 9] = re * P0; sr[o + 10] = re * P1; sr[o + 11] = re * P2;
+            sr[o + 12] = R(0.5) * inv_s;
+            sr[o + 13] = hz * rz;
+            sr[o + 14] = he * re;
+            sr[o + 15] = x->E * y->E * r;             // Theta with contraction coefficients
+            sr[o + 16] = hz;
+            sr[o + 17] = he;
           }
         }
         __syncwarp();
-        // ---- b. roots, weights and 2D integrals per (primitive, root)
+        // ---- b. roots, weights (FP64) and 2D integrals (R) per (primitive, root)
         for (int tk = tl; tk < bp * N; tk += TS) {
           const int j = tk / N, n = tk - (tk / N) * N;
           if (j < nbt) {
-            const int o = S_PRIM + j * NPS;
-            double u, w;
-            rys_root(a.rys_coef, a.rys_au, a.rys_aw, N, (int)__double_as_longlong(sm[o + 21]), sm[o + 18],
-                     sm[o + 19], sm[o + 20], n, u, w);
-            const double B00 = u * sm[o + 12];
-            const double B10 = fma(-u, sm[o + 15], sm[o + 13]);
-            const double B01 = fma(-u, sm[o + 16], sm[o + 14]);
-            const double wt = w * sm[o + 17];
-            const double C[3] = {fma(-u, sm[o + 6], sm[o + 0]), fma(-u, sm[o + 7], sm[o + 1]),
-                                 fma(-u, sm[o + 8], sm[o + 2])};
-            const double Cp[3] = {fma(u, sm[o + 9], sm[o + 3]), fma(u, sm[o + 10], sm[o + 4]),
-                                  fma(u, sm[o + 11], sm[o + 5])};
+            const int od = j * NPD, o = j * NPR;
+            double ud, wd;
+            rys_root(a.rys_coef, a.rys_au, a.rys_aw, N, (int)__double_as_longlong(sd[od + 3]), sd[od + 0],
+                     sd[od + 1], sd[od + 2], n, ud, wd);
+            const R u = (R)ud, w = (R)wd;
+            const R B00 = u * sr[o + 12];
+            const R B10 = fma(-u, sr[o + 13], sr[o + 16]);
+            const R B01 = fma(-u, sr[o + 14], sr[o + 17]);
+            const R wt = w * sr[o + 15];
+            const R C[3] = {fma(-u, sr[o + 6], sr[o + 0]), fma(-u, sr[o + 7], sr[o + 1]),
+                            fma(-u, sr[o + 8], sr[o + 2])};
+            const R Cp[3] = {fma(u, sr[o + 9], sr[o + 3]), fma(u, sr[o + 10], sr[o + 4]),
+                             fma(u, sr[o + 11], sr[o + 5])};
             const int g0 = S_2D + ((j * 3 + 0) * N + n) * nI;
             const int og[3] = {g0, g0 + N * nI, g0 + 2 * N * nI};
-            rys_2d3(sm, og, Le, Lf, wt, C, Cp, B00, B10, B01);
+            rys_2d3<R>(sr, og, Le, Lf, wt, C, Cp, B00, B10, B01);
           }
         }
         __syncwarp();
@@ -358,9 +318,9 @@ __global__ void __launch_bounds__(TPB) eri_class_kernel(const KernelArgs a) {
 #pragma unroll
               for (int k = 0; k < GSLOTS; ++k) {
                 if (k < kcnt) {
-                  const uint32_t p = pkd[k];
-                  const double v = sm[gx + (int)(p & 0xffu)] * sm[gy + (int)((p >> 8) & 0xffu)];
-                  acc[k] = fma(v, sm[gz + (int)((p >> 16) & 0xffu)], acc[k]);
+                  const uint32_t p = (TS == 1) ? __ldg(c.outidx + o0 + k) : pkd[k];
+                  const R v = sr[gx + (int)(p & 0xffu)] * sr[gy + (int)((p >> 8) & 0xffu)];
+                  acc[k] = fma(v, sr[gz + (int)((p >> 16) & 0xffu)], acc[k]);
                 }
               }
             }
@@ -379,109 +339,7 @@ __global__ void __launch_bounds__(TPB) eri_class_kernel(const KernelArgs a) {
     }
     __syncwarp();
 
-    // ---- 2. transfer relations: bra on e (vector over f), then ket on f (vector over ab)
-    const int nab = c.na * c.nb, ncd = c.nc * c.nd;
-    const double* Y = hrr_team(c.la, c.lb, AB, c.nf, E0, c.nf, 1, bufA, bufB, tl, TS, active);
-    const double* G = hrr_team(c.lc, c.ld, CD, nab, Y, 1, c.nf, bufA, bufB, tl, TS, active);
-    // (ab|cd) = G[ab*sab + cd*scd]
-    const int sab = (c.ld > 0) ? 1 : c.nf;
-    const int scd = (c.ld > 0) ? nab : 1;
-
-    // ---- 3. digestion / output
-    if (a.mode == KMODE_JK) {
-      if (active) {
-        double w = 1.0;
-        if (bra->sh0 == bra->sh1) w *= 0.5;
-        if (ket->sh0 == ket->sh1) w *= 0.5;
-        if (ib == ik) w *= 0.5;
-        const int p0 = bra->bf0, q0b = bra->bf1, r0 = ket->bf0, s0 = ket->bf1;
-        const int na = c.na, nb = c.nb, nc = c.nc, nd = c.nd;
-        const int nbf = a.nbf;
-        for (int xd = 0; xd < a.nD; ++xd) {
-          const double* Dx = a.D + (size_t)xd * nbf * nbf;
-          if (a.want & 1) {
-            double* Jx = a.J + (size_t)xd * nbf * nbf;
-            for (int t = tl; t < nab; t += TS) {
-              const int ia = t / nb, ibb = t - (t / nb) * nb;
-              double s = 0.0;
-              for (int cd = 0; cd < ncd; ++cd) {
-                const int ic = cd / nd, id = cd - (cd / nd) * nd;
-                s = fma(G[t * sab + cd * scd], __ldg(Dx + (size_t)(r0 + ic) * nbf + s0 + id), s);
-              }
-              atomicAdd(Jx + (size_t)(p0 + ia) * nbf + q0b + ibb, 2.0 * w * s);
-            }
-            for (int t = tl; t < ncd; t += TS) {
-              const int ic = t / nd, id = t - (t / nd) * nd;
-              double s = 0.0;
-              for (int ab = 0; ab < nab; ++ab) {
-                const int ia = ab / nb, ibb = ab - (ab / nb) * nb;
-                s = fma(G[ab * sab + t * scd], __ldg(Dx + (size_t)(p0 + ia) * nbf + q0b + ibb), s);
-              }
-              atomicAdd(Jx + (size_t)(r0 + ic) * nbf + s0 + id, 2.0 * w * s);
-            }
-          }
-          if (a.want & 2) {
-            double* Kx = a.K + (size_t)xd * nbf * nbf;
-            // K_ac += w sum_bd g D_bd
-            for (int t = tl; t < na * nc; t += TS) {
-              const int ia = t / nc, ic = t - (t / nc) * nc;
-              double s = 0.0;
-              for (int ibb = 0; ibb < nb; ++ibb)
-                for (int id = 0; id < nd; ++id)
-                  s = fma(G[(ia * nb + ibb) * sab + (ic * nd + id) * scd],
-                          __ldg(Dx + (size_t)(q0b + ibb) * nbf + s0 + id), s);
-              atomicAdd(Kx + (size_t)(p0 + ia) * nbf + r0 + ic, w * s);
-            }
-            // K_bd += w sum_ac g D_ac
-            for (int t = tl; t < nb * nd; t += TS) {
-              const int ibb = t / nd, id = t - (t / nd) * nd;
-              double s = 0.0;
-              for (int ia = 0; ia < na; ++ia)
-                for (int ic = 0; ic < nc; ++ic)
-                  s = fma(G[(ia * nb + ibb) * sab + (ic * nd + id) * scd],
-                          __ldg(Dx + (size_t)(p0 + ia) * nbf + r0 + ic), s);
-              atomicAdd(Kx + (size_t)(q0b + ibb) * nbf + s0 + id, w * s);
-            }
-            // K_ad += w sum_bc g D_bc
-            for (int t = tl; t < na * nd; t += TS) {
-              const int ia = t / nd, id = t - (t / nd) * nd;
-              double s = 0.0;
-              for (int ibb = 0; ibb < nb; ++ibb)
-                for (int ic = 0; ic < nc; ++ic)
-                  s = fma(G[(ia * nb + ibb) * sab + (ic * nd + id) * scd],
-                          __ldg(Dx + (size_t)(q0b + ibb) * nbf + r0 + ic), s);
-              atomicAdd(Kx + (size_t)(p0 + ia) * nbf + s0 + id, w * s);
-            }
-            // K_bc += w sum_ad g D_ad
-            for (int t = tl; t < nb * nc; t += TS) {
-              const int ibb = t / nc, ic = t - (t / nc) * nc;
-              double s = 0.0;
-              for (int ia = 0; ia < na; ++ia)
-                for (int id = 0; id < nd; ++id)
-                  s = fma(G[(ia * nb + ibb) * sab + (ic * nd + id) * scd],
-                          __ldg(Dx + (size_t)(p0 + ia) * nbf + s0 + id), s);
-              atomicAdd(Kx + (size_t)(q0b + ibb) * nbf + r0 + ic, w * s);
-            }
-          }
-        }
-      }
-    } else if (a.mode == KMODE_BLOCK) {
-      if (active) {
-        double* out = a.blockout + a.blockoff[task];
-        for (int t = tl; t < nab * ncd; t += TS) {
-          const int ab = t / ncd, cd = t - (t / ncd) * ncd;
-          out[t] = G[ab * sab + cd * scd];
-        }
-      }
-    } else {  // KMODE_SCHWARZ: bra and ket are the same pair; max_{a,b} |(ab|ab)|
-      double m = 0.0;
-      if (active)
-        for (int t = tl; t < nab; t += TS) m = fmax(m, fabs(G[t * sab + t * scd]));
-      if (TS > 1) {
-        for (int off = TS / 2; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
-      }
-      if (active && tl == 0) a.qout[task] = m;
-    }
+    finish_quartet<TS, R>(a, c, E0, bufA, bufB, tl, active, AB, CD, bra, ket, ib, ik, task);
     __syncwarp();
   }
   // ---- counters: one atomic pair per warp
@@ -574,31 +432,59 @@ extern "C" int erik_team_config(int ts, int* threads_per_block, int* max_g) {
   return (ts == 1 || ts == 8 || ts == 32) ? 0 : 1;
 }
 
-static const void* class_kernel_ptr(int ts) {
-  switch (ts) {
-    case 1: return (const void*)eri_class_kernel<1>;
-    case 8: return (const void*)eri_class_kernel<8>;
-    case 32: return (const void*)eri_class_kernel<32>;
+static const void* class_kernel_ptr(int ts, int fp32) {
+  if (fp32) {
+    switch (ts) {
+      case 1: return (const void*)eri_class_kernel<1, float>;
+      case 8: return (const void*)eri_class_kernel<8, float>;
+      case 32: return (const void*)eri_class_kernel<32, float>;
+    }
+  } else {
+    switch (ts) {
+      case 1: return (const void*)eri_class_kernel<1, double>;
+      case 8: return (const void*)eri_class_kernel<8, double>;
+      case 32: return (const void*)eri_class_kernel<32, double>;
+    }
   }
   return nullptr;
 }
 
-extern "C" int erik_blocks_per_sm(int ts, int smem_bytes, int* out) {
-  const void* k = class_kernel_ptr(ts);
+extern "C" int erik_blocks_per_sm(int ts, int fp32, int smem_bytes, int* out) {
+  const void* k = class_kernel_ptr(ts, fp32);
   if (!k) return (int)cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   if (e != cudaSuccess) return (int)e;
   return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k, TPB, smem_bytes);
 }
 
-extern "C" int erik_launch_class(int ts, const KernelArgs* a, int grid, int smem_bytes, void* stream) {
+extern "C" int erik_launch_class(int ts, int fp32, const KernelArgs* a, int grid, int smem_bytes, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
-  switch (ts) {
-    case 1: eri_class_kernel<1><<<grid, TPB, smem_bytes, s>>>(*a); break;
-    case 8: eri_class_kernel<8><<<grid, TPB, smem_bytes, s>>>(*a); break;
-    case 32: eri_class_kernel<32><<<grid, TPB, smem_bytes, s>>>(*a); break;
-    default: return (int)cudaErrorInvalidValue;
+  if (fp32) {
+    switch (ts) {
+      case 1: eri_class_kernel<1, float><<<grid, TPB, smem_bytes, s>>>(*a); break;
+      case 8: eri_class_kernel<8, float><<<grid, TPB, smem_bytes, s>>>(*a); break;
+      case 32: eri_class_kernel<32, float><<<grid, TPB, smem_bytes, s>>>(*a); break;
+      default: return (int)cudaErrorInvalidValue;
+    }
+  } else {
+    switch (ts) {
+      case 1: eri_class_kernel<1, double><<<grid, TPB, smem_bytes, s>>>(*a); break;
+      case 8: eri_class_kernel<8, double><<<grid, TPB, smem_bytes, s>>>(*a); break;
+      case 32: eri_class_kernel<32, double><<<grid, TPB, smem_bytes, s>>>(*a); break;
+      default: return (int)cudaErrorInvalidValue;
+    }
   }
+  return (int)cudaGetLastError();
+}
+
+extern "C" int erik_launch_compact(const KernelArgs* a, unsigned* tlist, unsigned long long cap,
+                                   unsigned long long* counts, unsigned* tiles, int mixed, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long ntiles = (a->ntask + CTILE - 1) / CTILE;
+  if (ntiles == 0) return (int)cudaMemsetAsync(counts, 0, 2 * sizeof(unsigned long long), st);
+  compact_count_kernel<<<(unsigned)ntiles, 256, 0, st>>>(*a, mixed, tiles);
+  compact_scan_kernel<<<1, 1024, 0, st>>>(tiles, ntiles, counts);
+  compact_write_kernel<<<(unsigned)ntiles, 256, 0, st>>>(*a, mixed, tiles, tlist, cap);
   return (int)cudaGetLastError();
 }
 

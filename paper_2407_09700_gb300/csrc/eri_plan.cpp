@@ -124,7 +124,8 @@ void make_class(int la, int lb, int lc, int ld, ClassDesc* c, int* ts, std::vect
     }
   *ts = choose_ts(c->nout);
   c->npass = (c->nout + *ts * 32 - 1) / (*ts * 32);
-  const int per_prim = 24 + 3 * c->nroots * c->nI;
+  // per primitive quartet: 4 doubles (table lookup) + 18 recurrence-type scalars + three 2D tables
+  const int per_prim = 4 + 18 + 3 * c->nroots * c->nI;
   if (*ts == 1) {
     c->bp = 1;
   } else {
@@ -132,6 +133,7 @@ void make_class(int la, int lb, int lc, int ld, ClassDesc* c, int* ts, std::vect
     c->bp = std::max(1, std::min(32, budget / per_prim));
   }
   c->team_doubles = c->bp * per_prim;
+  c->team_doubles_f32 = c->bp * 4 + (c->bp * (18 + 3 * c->nroots * c->nI) + 1) / 2;
   // HRR ping-pong size: max level size of the bra (vector nf) and ket (vector nab) passes
   long long m = 1;
   for (int k = 1; k <= lb; ++k) {
@@ -153,6 +155,7 @@ eri_status device_init(int dev, DeviceState** out) {
   DeviceState& s = g_dev[dev];
   if (!s.ready) {
     CUDA_TRY(erik_upload_cart_tables());
+    CUDA_TRY(erik_upload_cart_tables_small());
     size_t ncoef = (size_t)RYS_NCOEF, nas = (size_t)RYS_ASYM_OFFSET[RYS_NMAX] + RYS_NMAX;
     CUDA_TRY(cudaMalloc(&s.rys_coef, sizeof(double) * ncoef));
     CUDA_TRY(cudaMalloc(&s.rys_au, sizeof(double) * nas));
@@ -182,29 +185,31 @@ eri_status device_init(int dev, DeviceState** out) {
   return ERI_OK;
 }
 
-// FP64 operation count of the class kernel's algorithm (an FMA counts as 2), mirroring
-// eri_kernels.cu: per primitive quartet the Gaussian-product scalars and T, per root the
-// two degree-11 Horner sums and the recurrence coefficients, the three 2D tables, and the
-// Eq. 1 products (a multiply and an FMA per [e0|f0] value and root); per contracted
-// quartet the transfer relations and the six digestion updates.
-void class_model_flops(const ClassDesc& c, int nD, int want, double* per_prim, double* per_quartet) {
+// Operation count of the class kernel's algorithm (an FMA counts as 2), mirroring
+// eri_kernels.cu, split by pipe: per primitive quartet the Gaussian-product scalars and T,
+// per root the two degree-11 Horner sums (FP64 always) and the recurrence coefficients,
+// the three 2D tables and the Eq. 1 products (a multiply and an FMA per [e0|f0] value and
+// root); per contracted quartet the transfer relations and the six digestion updates (FP64
+// always).  fp32 = 1 counts the FP32 path of the mixed mode.
+void class_model_flops2(const ClassDesc& c, int nD, int want, int fp32, double* prim64, double* prim32,
+                        double* quart64, double* quart32) {
   const int N = c.nroots, Le = c.Le, Lf = c.Lf;
-  // scalars: s, rsqrt (4 ops), r^2, PQ (3), rz, re, T (1 + 5 + 1), locate (3), 6 scaled PQ, hs,
-  // hz*rz, he*re, Theta (2)
-  const double setup = 1 + 4 + 1 + 3 + 2 + 7 + 3 + 6 + 1 + 2 + 2;
-  const double root = 2 * 22.0 + 1 + 2 + 2 + 1 + 6 + 6;
-  double mult = 0.0, vrr = 0.0;                       // running multiples; three axes
-  if (Le >= 1) vrr += 1;                              // z: C00 * I0z
-  vrr += 3 * 3.0 * std::max(0, Le - 1);               // fma(C, I, nb10 * I)
+  const double t_setup = 1 + 4 + 3 + 8 + 3;            // s, rsqrt, PQ, T, table lookup (FP64)
+  const double r_setup = 1 + 2 + 6 + 1 + 2 + 2;        // r^2, rz, re, scaled PQ, hs, hz*rz, he*re, Theta
+  const double horner = 2 * 22.0;
+  const double coef = 1 + 2 + 2 + 1 + 6 + 6;
+  double mult = 0.0, vrr = 0.0;                        // running multiples; three axes
+  if (Le >= 1) vrr += 1;                               // z: C00 * I0z
+  vrr += 3 * 3.0 * std::max(0, Le - 1);                // fma(C, I, nb10 * I)
   mult += std::max(0, Le - 1);
   if (Lf >= 1) {
-    vrr += 1;                                         // z: C00' * I0z
-    vrr += 3 * 3.0 * (Lf - 1);                        // row 0
+    vrr += 1;                                          // z: C00' * I0z
+    vrr += 3 * 3.0 * (Lf - 1);                         // row 0
     mult += Lf - 1;
-    vrr += Le * (3 * 3.0 + 3 * 5.0 * (Lf - 1));       // rows 1..Le
+    vrr += Le * (3 * 3.0 + 3 * 5.0 * (Lf - 1));        // rows 1..Le
     mult += Le * (Lf - 1) + Le;
   }
-  *per_prim = setup + N * (root + mult + vrr) + 3.0 * N * c.nout;
+  const double rec = N * (coef + mult + vrr) + 3.0 * N * c.nout;
   double hrr = 0.0;
   for (int k = 1; k <= c.lb; ++k)
     hrr += 2.0 * (cart_below(c.la + c.lb - k + 1) - cart_below(c.la)) * ncart(k) * c.nf;
@@ -212,7 +217,24 @@ void class_model_flops(const ClassDesc& c, int nD, int want, double* per_prim, d
     hrr += 2.0 * (cart_below(c.lc + c.ld - k + 1) - cart_below(c.lc)) * ncart(k) * c.na * c.nb;
   const double nabcd = (double)c.na * c.nb * c.nc * c.nd;
   const double dig = 2.0 * nabcd * nD * (((want & 1) ? 2 : 0) + ((want & 2) ? 4 : 0));
-  *per_quartet = hrr + dig;
+  if (fp32) {
+    *prim64 = t_setup + N * horner;
+    *prim32 = r_setup + 4 + rec;                       // + FP32 rsqrt and PQ
+    *quart64 = dig;
+    *quart32 = hrr;
+  } else {
+    *prim64 = t_setup + r_setup + N * horner + rec;
+    *prim32 = 0.0;
+    *quart64 = hrr + dig;
+    *quart32 = 0.0;
+  }
+}
+
+void class_model_flops(const ClassDesc& c, int nD, int want, double* per_prim, double* per_quartet) {
+  double a, b, q, r;
+  class_model_flops2(c, nD, want, 0, &a, &b, &q, &r);
+  *per_prim = a + b;
+  *per_quartet = q + r;
 }
 
 void normalise(int nshell, const int* l, const int* nprim, const int* off, const double* exps,
@@ -260,11 +282,12 @@ struct eri_plan {
   ShellPair* d_pairs_all = nullptr;
   ShellPair* d_pairs = nullptr;
   PrimPair* d_prims = nullptr;
+  PrimPairF* d_primsf = nullptr;
   int* d_sh_bf0 = nullptr;
   int* d_sh_n = nullptr;
   double* d_Dmax = nullptr;
   unsigned long long* d_counters = nullptr;   // one per class launch
-  unsigned long long* d_stats = nullptr;      // [225][2]
+  unsigned long long* d_stats = nullptr;      // [2][256][2]: FP64 launches, then FP32 launches
   double* d_scratch = nullptr;
   size_t scratch_doubles = 0;
   int* d_tasks = nullptr;
@@ -274,6 +297,11 @@ struct eri_plan {
   long long* d_off = nullptr;
   size_t off_cap = 0;
   double* d_host_io = nullptr;                // D, J, K staging for eri_jk_host
+  unsigned* d_tlist = nullptr;                // compacted task lists (largest class)
+  size_t tlist_cap = 0;
+  unsigned long long* d_tcount = nullptr;     // [256][2] FP64 / FP32 list lengths
+  unsigned* d_tiles = nullptr;                // per-tile counts / offsets of the compaction
+  size_t tiles_cap = 0;
   size_t host_io_cap = 0;
   cudaStream_t last_stream = nullptr;
   // last eri_jk bookkeeping
@@ -283,7 +311,7 @@ struct eri_plan {
   bool profiling = false;
   std::vector<cudaEvent_t> events;            // 2 per launch
   std::vector<int> last_launch_xy;            // X*15+Y per launch
-  std::vector<int> last_launch_ts, last_launch_grid;
+  std::vector<int> last_launch_ts, last_launch_grid, last_launch_fp32, last_launch_small;
 };
 
 namespace {
@@ -316,15 +344,15 @@ eri_status ensure_buf(T** ptr, size_t* cap, size_t n) {
 }
 
 // Grid and dynamic shared memory for one class launch.
-eri_status launch_shape(eri_plan* p, int X, int Y, long long nteams_needed, int* grid, int* smem,
+eri_status launch_shape(eri_plan* p, int X, int Y, int fp32, long long nteams_needed, int* grid, int* smem,
                         int* ts_out) {
   const ClassDesc& c = p->dev->classes[X][Y];
   const int ts = p->dev->ts[X][Y];
   const int teams_per_block = 128 / ts;
-  *smem = (int)(sizeof(double) * (size_t)c.team_doubles * teams_per_block);
+  *smem = (int)(sizeof(double) * (size_t)(fp32 ? c.team_doubles_f32 : c.team_doubles) * teams_per_block);
   if (*smem > 200 * 1024) return fail(ERI_ERR_ARG, "class (%d%d|%d%d) needs %d bytes of shared memory", c.la, c.lb, c.lc, c.ld, *smem);
   int bps = 0;
-  CUDA_TRY(erik_blocks_per_sm(ts, *smem, &bps));
+  CUDA_TRY(erik_blocks_per_sm(ts, fp32, *smem, &bps));
   if (bps < 1) bps = 1;
   long long full = (long long)p->dev->sms * bps;
   long long need = (nteams_needed + teams_per_block - 1) / teams_per_block;
@@ -338,6 +366,7 @@ KernelArgs base_args(eri_plan* p, int X, int Y) {
   memset(&a, 0, sizeof(a));
   a.c = p->dev->classes[X][Y];
   a.prims = p->d_prims;
+  a.primsf = p->d_primsf;
   a.nsh = p->nshell;
   a.nbf = p->nbf;
   const int N = a.c.nroots;
@@ -359,7 +388,7 @@ eri_status run_explicit(eri_plan* p, int X, int Y, int mode, const std::vector<i
   if ((s = ensure_buf(&p->d_out, &p->out_cap, std::max<size_t>(out_doubles, 1))) != ERI_OK) return s;
   if (mode == KMODE_BLOCK && (s = ensure_buf(&p->d_off, &p->off_cap, offs.size())) != ERI_OK) return s;
   int grid, smem, ts;
-  if ((s = launch_shape(p, X, Y, nt, &grid, &smem, &ts)) != ERI_OK) return s;
+  if ((s = launch_shape(p, X, Y, 0, nt, &grid, &smem, &ts)) != ERI_OK) return s;
   const ClassDesc& c = p->dev->classes[X][Y];
   size_t need = (size_t)grid * (size_t)(128 / ts) * (size_t)c.scratch_per_team;
   if ((s = ensure_scratch(p, need)) != ERI_OK) return s;
@@ -378,7 +407,7 @@ eri_status run_explicit(eri_plan* p, int X, int Y, int mode, const std::vector<i
   a.counter = p->d_counters;
   a.scratch = p->d_scratch;
   a.stats = nullptr;
-  CUDA_TRY(erik_launch_class(ts, &a, grid, smem, st));
+  CUDA_TRY(erik_launch_class(ts, 0, &a, grid, smem, st));
   return ERI_OK;
 }
 
@@ -405,6 +434,156 @@ eri_status validate_basis(const eri_basis* b) {
   return ERI_OK;
 }
 
+
+// ---------------------------------------------------------------- J/K launch machinery
+struct Launch {
+  int X, Y, fp32, grid, smem, ts;
+  long long nt;
+  int small;             // 1: compile-time specialised kernel (eri_small.cu)
+};
+
+eri_status check_jk_args(eri_plan* p, const double* D, int nD, double* J, double* K, int flags) {
+  if (!p) return fail(ERI_ERR_ARG, "plan is NULL");
+  if (!D) return fail(ERI_ERR_ARG, "D is NULL");
+  if (nD < 1 || nD > p->opts.max_nd) return fail(ERI_ERR_ARG, "nD = %d outside [1, %d]", nD, p->opts.max_nd);
+  const int want = flags & 3;
+  if (want == 0) return fail(ERI_ERR_ARG, "flags request neither J nor K");
+  if ((want & 1) && !J) return fail(ERI_ERR_ARG, "J requested but NULL");
+  if ((want & 2) && !K) return fail(ERI_ERR_ARG, "K requested but NULL");
+  return ERI_OK;
+}
+
+// One launch per class (pair-type pair X >= Y); in the mixed mode one FP64 and one FP32
+// launch per class.  Grids are capped so that grid * teams * scratch <= max_scratch when
+// max_scratch > 0.
+eri_status plan_launches(eri_plan* p, size_t max_scratch, std::vector<Launch>* out) {
+  out->clear();
+  const int nprec = (p->opts.precision == ERI_MIXED) ? 2 : 1;
+  for (int X = 0; X < ERI_NPAIRTYPE; ++X) {
+    if (!p->type_cnt[X]) continue;
+    for (int Y = 0; Y <= X; ++Y) {
+      if (!p->type_cnt[Y]) continue;
+      const long long nx = p->type_cnt[X], ny = p->type_cnt[Y];
+      const long long nt = (X == Y) ? nx * (nx + 1) / 2 : nx * ny;
+      for (int fp32 = 0; fp32 < nprec; ++fp32) {
+        Launch l{X, Y, fp32, 0, 0, 0, nt, 0};
+        eri_status s = launch_shape(p, X, Y, fp32, nt, &l.grid, &l.smem, &l.ts);
+        if (s != ERI_OK) return s;
+        const ClassDesc& cd = p->dev->classes[X][Y];
+        if (l.ts == 1 && erik_small_available(cd.la, cd.lb, cd.lc, cd.ld)) {
+          int bps = 0;
+          CUDA_TRY(erik_small_blocks_per_sm(cd.la, cd.lb, cd.lc, cd.ld, fp32, &bps));
+          if (bps < 1) bps = 1;
+          const long long full = (long long)p->dev->sms * bps;
+          const long long need = (nt + 127) / 128;
+          l.grid = (int)std::max(1LL, std::min(full, need));
+          l.smem = 0;
+          l.small = 1;
+        }
+        if (max_scratch > 0) {
+          const ClassDesc& c = p->dev->classes[X][Y];
+          const size_t per_block = (size_t)(128 / l.ts) * (size_t)c.scratch_per_team;
+          if (per_block > max_scratch)
+            return fail(ERI_ERR_ARG,
+                        "class (%d%d|%d%d) needs %zu bytes of scratch for one block, more than the %zu-byte "
+                        "static scratch of eri_jk_noalloc",
+                        c.la, c.lb, c.lc, c.ld, per_block * sizeof(double), max_scratch * sizeof(double));
+          l.grid = (int)std::min<size_t>((size_t)l.grid, max_scratch / per_block);
+        }
+        out->push_back(l);
+      }
+    }
+  }
+  return ERI_OK;
+}
+
+// Density maxima, every class launch, symmetrisation.  Records launches for the profiler
+// when record is set.  Allocates nothing except profiling events when record is set.
+eri_status run_jk(eri_plan* p, const std::vector<Launch>& launches, const double* D, int nD, double* J, double* K,
+                  int want, cudaStream_t st, double* scratch, bool record, bool use_lists) {
+  const size_t mat = (size_t)nD * p->nbf * p->nbf;
+  if (want & 1) CUDA_TRY(cudaMemsetAsync(J, 0, sizeof(double) * mat, st));
+  if (want & 2) CUDA_TRY(cudaMemsetAsync(K, 0, sizeof(double) * mat, st));
+  CUDA_TRY(erik_launch_dmax(D, nD, p->nbf, p->nshell, p->d_sh_bf0, p->d_sh_n, p->d_Dmax, st));
+  CUDA_TRY(cudaMemsetAsync(p->d_counters, 0, sizeof(unsigned long long) * 256, st));
+  CUDA_TRY(cudaMemsetAsync(p->d_stats, 0, sizeof(unsigned long long) * 4 * 256, st));
+  if (use_lists) CUDA_TRY(cudaMemsetAsync(p->d_tcount, 0, sizeof(unsigned long long) * 2 * 256, st));
+  const bool prof = record && p->profiling;
+  if (prof) {
+    while (p->events.size() < 2 * launches.size()) {
+      cudaEvent_t e;
+      CUDA_TRY(cudaEventCreate(&e));
+      p->events.push_back(e);
+    }
+  }
+  if (record) {
+    p->last_launch_xy.clear();
+    p->last_launch_ts.clear();
+    p->last_launch_grid.clear();
+    p->last_launch_fp32.clear();
+    p->last_launch_small.clear();
+  }
+  long long cand = 0;
+  int li = 0, ci = -1;
+  const bool mixed = p->opts.precision == ERI_MIXED;
+  for (const Launch& l : launches) {
+    const bool listed = use_lists && (unsigned long long)l.nt <= 0xffffffffULL && (size_t)l.nt <= p->tlist_cap;
+    KernelArgs a = base_args(p, l.X, l.Y);
+    a.pairs = p->d_pairs;
+    a.bra0 = p->type_off[l.X];
+    a.nbra = p->type_cnt[l.X];
+    a.ket0 = p->type_off[l.Y];
+    a.nket = p->type_cnt[l.Y];
+    a.tri = (l.X == l.Y);
+    a.ntask = l.nt;
+    a.Dmax = p->d_Dmax;
+    a.tau = p->opts.screen_thresh;
+    a.prec_sel = mixed ? (l.fp32 ? 2 : 1) : 0;
+    a.mixed_thr = p->opts.mixed_thresh;
+    a.D = D;
+    a.J = J;
+    a.K = K;
+    a.nD = nD;
+    a.want = want;
+    a.mode = KMODE_JK;
+    a.counter = p->d_counters + li;
+    a.scratch = scratch;
+    a.stats = p->d_stats + 2 * (256 * l.fp32 + l.X * ERI_NPAIRTYPE + l.Y);
+    if (!l.fp32) ++ci;
+    if (listed) {
+      unsigned long long* cnt = p->d_tcount + 2 * ci;
+      if (!l.fp32)
+        CUDA_TRY(erik_launch_compact(&a, p->d_tlist, (unsigned long long)l.nt, cnt, p->d_tiles, mixed ? 1 : 0, st));
+      a.tlist = p->d_tlist;
+      a.list_cap = (unsigned long long)l.nt;
+      a.from_back = l.fp32;
+      a.tcount = cnt + l.fp32;
+    }
+    if (prof) CUDA_TRY(cudaEventRecord(p->events[2 * li], st));
+    if (l.small)
+      CUDA_TRY(erik_launch_small(a.c.la, a.c.lb, a.c.lc, a.c.ld, l.fp32, &a, l.grid, st));
+    else
+      CUDA_TRY(erik_launch_class(l.ts, l.fp32, &a, l.grid, l.smem, st));
+    if (prof) CUDA_TRY(cudaEventRecord(p->events[2 * li + 1], st));
+    if (record) {
+      p->last_launch_xy.push_back(l.X * ERI_NPAIRTYPE + l.Y);
+      p->last_launch_ts.push_back(l.ts);
+      p->last_launch_grid.push_back(l.grid);
+      p->last_launch_fp32.push_back(l.fp32);
+      p->last_launch_small.push_back(l.small);
+    }
+    if (!l.fp32) cand += l.nt;
+    ++li;
+  }
+  if (want & 1) CUDA_TRY(erik_launch_symmetrize(J, nD, p->nbf, st));
+  if (want & 2) CUDA_TRY(erik_launch_symmetrize(K, nD, p->nbf, st));
+  p->last_stream = st;
+  p->last_candidates = cand;
+  p->last_nclasses = (int)launches.size();
+  p->last_nD = nD;
+  p->last_want = want;
+  return ERI_OK;
+}
 }  // namespace
 
 // ================================================================= C-ABI
@@ -419,8 +598,9 @@ eri_status eri_plan_destroy(eri_plan* p) {
   cudaSetDevice(p->device);
   cudaDeviceSynchronize();
   for (cudaEvent_t e : p->events) cudaEventDestroy(e);
-  void* bufs[] = {p->d_pairs_all, p->d_pairs, p->d_prims, p->d_sh_bf0, p->d_sh_n, p->d_Dmax, p->d_counters,
-                  p->d_stats, p->d_scratch, p->d_tasks, p->d_out, p->d_off, p->d_host_io};
+  void* bufs[] = {p->d_pairs_all, p->d_pairs, p->d_prims, p->d_primsf, p->d_sh_bf0, p->d_sh_n, p->d_Dmax, p->d_counters,
+                  p->d_stats, p->d_scratch, p->d_tasks, p->d_out, p->d_off, p->d_host_io, p->d_tlist,
+                  p->d_tcount, p->d_tiles};
   for (void* b : bufs)
     if (b) cudaFree(b);
   delete p;
@@ -529,11 +709,13 @@ eri_status eri_plan_create(const eri_basis* basis, const eri_opts* opts, void* c
   if (cudaMalloc(&p->d_pairs_all, sizeof(ShellPair) * npair) != cudaSuccess ||
       cudaMalloc(&p->d_pairs, sizeof(ShellPair) * npair) != cudaSuccess ||
       cudaMalloc(&p->d_prims, sizeof(PrimPair) * p->prims.size()) != cudaSuccess ||
+      cudaMalloc(&p->d_primsf, sizeof(PrimPairF) * p->prims.size()) != cudaSuccess ||
       cudaMalloc(&p->d_sh_bf0, sizeof(int) * p->nshell) != cudaSuccess ||
       cudaMalloc(&p->d_sh_n, sizeof(int) * p->nshell) != cudaSuccess ||
       cudaMalloc(&p->d_Dmax, sizeof(double) * p->nshell * p->nshell) != cudaSuccess ||
       cudaMalloc(&p->d_counters, sizeof(unsigned long long) * 256) != cudaSuccess ||
-      cudaMalloc(&p->d_stats, sizeof(unsigned long long) * 2 * 256) != cudaSuccess) {
+      cudaMalloc(&p->d_stats, sizeof(unsigned long long) * 4 * 256) != cudaSuccess ||
+      cudaMalloc(&p->d_tcount, sizeof(unsigned long long) * 2 * 256) != cudaSuccess) {
     cudaGetLastError();
     return cleanup(fail(ERI_ERR_OOM, "device allocation failed in eri_plan_create"));
   }
@@ -545,9 +727,23 @@ eri_status eri_plan_create(const eri_basis* basis, const eri_opts* opts, void* c
   } while (0)
   PLAN_TRY(cudaMemcpyAsync(p->d_pairs_all, p->pairs_all.data(), sizeof(ShellPair) * npair, cudaMemcpyHostToDevice, st));
   PLAN_TRY(cudaMemcpyAsync(p->d_prims, p->prims.data(), sizeof(PrimPair) * p->prims.size(), cudaMemcpyHostToDevice, st));
+  std::vector<PrimPairF> primsf(p->prims.size());
+  for (size_t k = 0; k < p->prims.size(); ++k) {
+    const PrimPair& x = p->prims[k];
+    PrimPairF& f = primsf[k];
+    f.zeta = (float)x.zeta;
+    for (int c = 0; c < 3; ++c) {
+      f.P[c] = (float)x.P[c];
+      f.PA[c] = (float)x.PA[c];
+    }
+    f.E = (float)x.E;
+    f.hz = (float)x.hz;
+    f.pad = 0.f;
+  }
+  PLAN_TRY(cudaMemcpy(p->d_primsf, primsf.data(), sizeof(PrimPairF) * primsf.size(), cudaMemcpyHostToDevice));
   PLAN_TRY(cudaMemcpyAsync(p->d_sh_bf0, p->sh_bf0.data(), sizeof(int) * p->nshell, cudaMemcpyHostToDevice, st));
   PLAN_TRY(cudaMemcpyAsync(p->d_sh_n, sh_n.data(), sizeof(int) * p->nshell, cudaMemcpyHostToDevice, st));
-  PLAN_TRY(cudaMemsetAsync(p->d_stats, 0, sizeof(unsigned long long) * 2 * 256, st));
+  PLAN_TRY(cudaMemsetAsync(p->d_stats, 0, sizeof(unsigned long long) * 4 * 256, st));
 
   // ---- Schwarz factors (Eq. 7) from the diagonal quartets (ij|ij), one class (X|X) at a time
   p->Q.assign((size_t)p->nshell * p->nshell, 0.0);
@@ -590,89 +786,20 @@ eri_status eri_plan_create(const eri_basis* basis, const eri_opts* opts, void* c
 
 eri_status eri_jk(eri_plan* p, const double* D, int nD, double* J, double* K, int flags, void* cuda_stream) {
   g_err.clear();
-  if (!p) return fail(ERI_ERR_ARG, "plan is NULL");
-  if (!D) return fail(ERI_ERR_ARG, "D is NULL");
-  if (nD < 1 || nD > p->opts.max_nd) return fail(ERI_ERR_ARG, "nD = %d outside [1, %d]", nD, p->opts.max_nd);
-  const int want = flags & 3;
-  if (want == 0) return fail(ERI_ERR_ARG, "flags request neither J nor K");
-  if ((want & 1) && !J) return fail(ERI_ERR_ARG, "J requested but NULL");
-  if ((want & 2) && !K) return fail(ERI_ERR_ARG, "K requested but NULL");
-  cudaStream_t st = (cudaStream_t)cuda_stream;
-  const size_t mat = (size_t)nD * p->nbf * p->nbf;
-  if (want & 1) CUDA_TRY(cudaMemsetAsync(J, 0, sizeof(double) * mat, st));
-  if (want & 2) CUDA_TRY(cudaMemsetAsync(K, 0, sizeof(double) * mat, st));
-  CUDA_TRY(erik_launch_dmax(D, nD, p->nbf, p->nshell, p->d_sh_bf0, p->d_sh_n, p->d_Dmax, st));
-  CUDA_TRY(cudaMemsetAsync(p->d_counters, 0, sizeof(unsigned long long) * 256, st));
-  CUDA_TRY(cudaMemsetAsync(p->d_stats, 0, sizeof(unsigned long long) * 2 * 256, st));
-
-  // scratch for the largest class launch
-  struct L { int X, Y, grid, smem, ts; long long nt; };
-  std::vector<L> launches;
-  size_t need = 0;
-  long long cand = 0;
-  for (int X = 0; X < ERI_NPAIRTYPE; ++X) {
-    if (!p->type_cnt[X]) continue;
-    for (int Y = 0; Y <= X; ++Y) {
-      if (!p->type_cnt[Y]) continue;
-      const long long nx = p->type_cnt[X], ny = p->type_cnt[Y];
-      const long long nt = (X == Y) ? nx * (nx + 1) / 2 : nx * ny;
-      L l{X, Y, 0, 0, 0, nt};
-      eri_status s = launch_shape(p, X, Y, nt, &l.grid, &l.smem, &l.ts);
-      if (s != ERI_OK) return s;
-      need = std::max(need, (size_t)l.grid * (size_t)(128 / l.ts) * (size_t)p->dev->classes[X][Y].scratch_per_team);
-      launches.push_back(l);
-      cand += nt;
-    }
-  }
-  eri_status s = ensure_scratch(p, need);
+  eri_status s = check_jk_args(p, D, nD, J, K, flags);
   if (s != ERI_OK) return s;
-  if (p->profiling) {
-    while (p->events.size() < 2 * launches.size()) {
-      cudaEvent_t e;
-      CUDA_TRY(cudaEventCreate(&e));
-      p->events.push_back(e);
-    }
-  }
-  p->last_launch_xy.clear();
-  p->last_launch_ts.clear();
-  p->last_launch_grid.clear();
-  int li = 0;
-  for (const L& l : launches) {
-    KernelArgs a = base_args(p, l.X, l.Y);
-    a.pairs = p->d_pairs;
-    a.bra0 = p->type_off[l.X];
-    a.nbra = p->type_cnt[l.X];
-    a.ket0 = p->type_off[l.Y];
-    a.nket = p->type_cnt[l.Y];
-    a.tri = (l.X == l.Y);
-    a.ntask = l.nt;
-    a.Dmax = p->d_Dmax;
-    a.tau = p->opts.screen_thresh;
-    a.D = D;
-    a.J = J;
-    a.K = K;
-    a.nD = nD;
-    a.want = want;
-    a.mode = KMODE_JK;
-    a.counter = p->d_counters + li;
-    a.scratch = p->d_scratch;
-    a.stats = p->d_stats + 2 * (l.X * ERI_NPAIRTYPE + l.Y);
-    if (p->profiling) CUDA_TRY(cudaEventRecord(p->events[2 * li], st));
-    CUDA_TRY(erik_launch_class(l.ts, &a, l.grid, l.smem, st));
-    if (p->profiling) CUDA_TRY(cudaEventRecord(p->events[2 * li + 1], st));
-    p->last_launch_xy.push_back(l.X * ERI_NPAIRTYPE + l.Y);
-    p->last_launch_ts.push_back(l.ts);
-    p->last_launch_grid.push_back(l.grid);
-    ++li;
-  }
-  if (want & 1) CUDA_TRY(erik_launch_symmetrize(J, nD, p->nbf, st));
-  if (want & 2) CUDA_TRY(erik_launch_symmetrize(K, nD, p->nbf, st));
-  p->last_stream = st;
-  p->last_candidates = cand;
-  p->last_nclasses = (int)launches.size();
-  p->last_nD = nD;
-  p->last_want = want;
-  return ERI_OK;
+  std::vector<Launch> launches;
+  if ((s = plan_launches(p, 0, &launches)) != ERI_OK) return s;
+  size_t need = 0;
+  for (const Launch& l : launches)
+    need = std::max(need, (size_t)l.grid * (size_t)(128 / l.ts) * (size_t)p->dev->classes[l.X][l.Y].scratch_per_team);
+  if ((s = ensure_scratch(p, need)) != ERI_OK) return s;
+  size_t maxnt = 1;
+  for (const Launch& l : launches)
+    if ((unsigned long long)l.nt <= 0xffffffffULL) maxnt = std::max(maxnt, (size_t)l.nt);
+  if ((s = ensure_buf(&p->d_tlist, &p->tlist_cap, maxnt)) != ERI_OK) return s;
+  if ((s = ensure_buf(&p->d_tiles, &p->tiles_cap, 2 * ((maxnt + 1023) / 1024 + 1))) != ERI_OK) return s;
+  return run_jk(p, launches, D, nD, J, K, flags & 3, (cudaStream_t)cuda_stream, p->d_scratch, true, true);
 }
 
 eri_status eri_jk_host(eri_plan* p, const double* D, int nD, double* J, double* K, int flags, void* cuda_stream) {
@@ -780,19 +907,23 @@ eri_status eri_flop_stats(eri_plan* p, eri_stats* out) {
   g_err.clear();
   if (!p || !out) return fail(ERI_ERR_ARG, "plan or out is NULL");
   CUDA_TRY(cudaStreamSynchronize(p->last_stream));
-  std::vector<unsigned long long> st(2 * 256);
-  CUDA_TRY(cudaMemcpy(st.data(), p->d_stats, sizeof(unsigned long long) * 2 * 256, cudaMemcpyDeviceToHost));
+  std::vector<unsigned long long> st(4 * 256);
+  CUDA_TRY(cudaMemcpy(st.data(), p->d_stats, sizeof(unsigned long long) * 4 * 256, cudaMemcpyDeviceToHost));
   memset(out, 0, sizeof(*out));
   out->quartets_candidate = p->last_candidates;
-  for (int X = 0; X < ERI_NPAIRTYPE; ++X)
-    for (int Y = 0; Y < ERI_NPAIRTYPE; ++Y) {
-      const unsigned long long q = st[2 * (X * ERI_NPAIRTYPE + Y)], pq = st[2 * (X * ERI_NPAIRTYPE + Y) + 1];
-      out->quartets_computed += (long long)q;
-      out->prim_quartets += (long long)pq;
-      double fp, fq;
-      class_model_flops(p->dev->classes[X][Y], p->last_nD, p->last_want, &fp, &fq);
-      out->model_flops += fp * (double)pq + fq * (double)q;
-    }
+  for (int f = 0; f < 2; ++f)
+    for (int X = 0; X < ERI_NPAIRTYPE; ++X)
+      for (int Y = 0; Y < ERI_NPAIRTYPE; ++Y) {
+        const size_t k = 2 * (256 * f + X * ERI_NPAIRTYPE + Y);
+        const unsigned long long q = st[k], pq = st[k + 1];
+        out->quartets_computed += (long long)q;
+        out->prim_quartets += (long long)pq;
+        if (f) out->quartets_fp32 += (long long)q;
+        double a64, a32, q64, q32;
+        class_model_flops2(p->dev->classes[X][Y], p->last_nD, p->last_want, f, &a64, &a32, &q64, &q32);
+        out->model_flops += (a64 + a32) * (double)pq + (q64 + q32) * (double)q;
+        out->model_flops_fp32 += a32 * (double)pq + q32 * (double)q;
+      }
   out->npairs_total = (int)p->pairs_all.size();
   out->npairs_kept = p->npairs_kept;
   out->nclasses_launched = p->last_nclasses;
@@ -814,10 +945,11 @@ eri_status eri_launch_records(eri_plan* p, eri_launch_record* out, int cap, int*
   const int nl = (int)p->last_launch_xy.size();
   *n = nl;
   if (nl == 0) return ERI_OK;
-  std::vector<unsigned long long> st(2 * 256);
-  CUDA_TRY(cudaMemcpy(st.data(), p->d_stats, sizeof(unsigned long long) * 2 * 256, cudaMemcpyDeviceToHost));
+  std::vector<unsigned long long> st(4 * 256);
+  CUDA_TRY(cudaMemcpy(st.data(), p->d_stats, sizeof(unsigned long long) * 4 * 256, cudaMemcpyDeviceToHost));
   for (int i = 0; i < nl && i < cap; ++i) {
     const int xy = p->last_launch_xy[i];
+    const int f = p->last_launch_fp32[i];
     const ClassDesc& c = p->dev->classes[xy / ERI_NPAIRTYPE][xy % ERI_NPAIRTYPE];
     eri_launch_record& r = out[i];
     r.la = c.la; r.lb = c.lb; r.lc = c.lc; r.ld = c.ld;
@@ -826,11 +958,14 @@ eri_status eri_launch_records(eri_plan* p, eri_launch_record* out, int cap, int*
     float ms = 0.f;
     CUDA_TRY(cudaEventElapsedTime(&ms, p->events[2 * i], p->events[2 * i + 1]));
     r.ms = ms;
-    r.quartets = (long long)st[2 * xy];
-    r.prim_quartets = (long long)st[2 * xy + 1];
-    double fp, fq;
-    class_model_flops(c, p->last_nD, p->last_want, &fp, &fq);
-    r.model_flops = fp * (double)r.prim_quartets + fq * (double)r.quartets;
+    r.quartets = (long long)st[2 * (256 * f + xy)];
+    r.prim_quartets = (long long)st[2 * (256 * f + xy) + 1];
+    double a64, a32, q64, q32;
+    class_model_flops2(c, p->last_nD, p->last_want, f, &a64, &a32, &q64, &q32);
+    r.model_flops = (a64 + a32) * (double)r.prim_quartets + (q64 + q32) * (double)r.quartets;
+    r.model_flops_fp32 = a32 * (double)r.prim_quartets + q32 * (double)r.quartets;
+    r.fp32 = f;
+    r.specialised = p->last_launch_small[i];
   }
   return ERI_OK;
 }
@@ -860,77 +995,15 @@ extern "C" __attribute__((visibility("hidden"))) eri_status eri_internal_fail(er
 // occupancy-limited grid); a class whose single block needs more than scratch_doubles is
 // rejected with ERI_ERR_ARG before anything is launched.
 extern "C" __attribute__((visibility("hidden"))) eri_status eri_internal_jk_fixed_scratch(
-    eri_plan* p, const double* D, int nD, double* J, double* K,
-                                                    int flags, void* cuda_stream, double* scratch,
-                                                    size_t scratch_doubles) {
+    eri_plan* p, const double* D, int nD, double* J, double* K, int flags, void* cuda_stream, double* scratch,
+    size_t scratch_doubles) {
   g_err.clear();
-  if (!p) return fail(ERI_ERR_ARG, "plan is NULL");
-  if (!D) return fail(ERI_ERR_ARG, "D is NULL");
-  if (nD < 1 || nD > p->opts.max_nd) return fail(ERI_ERR_ARG, "nD = %d outside [1, %d]", nD, p->opts.max_nd);
-  const int want = flags & 3;
-  if (want == 0) return fail(ERI_ERR_ARG, "flags request neither J nor K");
-  if ((want & 1) && !J) return fail(ERI_ERR_ARG, "J requested but NULL");
-  if ((want & 2) && !K) return fail(ERI_ERR_ARG, "K requested but NULL");
+  eri_status s = check_jk_args(p, D, nD, J, K, flags);
+  if (s != ERI_OK) return s;
   int cur = -1;
   CUDA_TRY(cudaGetDevice(&cur));
   if (cur != p->device) return fail(ERI_ERR_ARG, "the plan belongs to device %d but device %d is current", p->device, cur);
-  struct L { int X, Y, grid, smem, ts; long long nt; };
-  std::vector<L> launches;
-  long long cand = 0;
-  for (int X = 0; X < ERI_NPAIRTYPE; ++X) {
-    if (!p->type_cnt[X]) continue;
-    for (int Y = 0; Y <= X; ++Y) {
-      if (!p->type_cnt[Y]) continue;
-      const long long nx = p->type_cnt[X], ny = p->type_cnt[Y];
-      const long long nt = (X == Y) ? nx * (nx + 1) / 2 : nx * ny;
-      L l{X, Y, 0, 0, 0, nt};
-      eri_status s = launch_shape(p, X, Y, nt, &l.grid, &l.smem, &l.ts);
-      if (s != ERI_OK) return s;
-      const size_t per_block = (size_t)(128 / l.ts) * (size_t)p->dev->classes[X][Y].scratch_per_team;
-      if (per_block > scratch_doubles) {
-        const ClassDesc& c = p->dev->classes[X][Y];
-        return fail(ERI_ERR_ARG,
-                    "class (%d%d|%d%d) needs %zu bytes of scratch for one block, more than the %zu-byte "
-                    "static scratch of eri_jk_noalloc",
-                    c.la, c.lb, c.lc, c.ld, per_block * sizeof(double), scratch_doubles * sizeof(double));
-      }
-      l.grid = (int)std::min<size_t>((size_t)l.grid, scratch_doubles / per_block);
-      launches.push_back(l);
-      cand += nt;
-    }
-  }
-  cudaStream_t st = (cudaStream_t)cuda_stream;
-  const size_t mat = (size_t)nD * p->nbf * p->nbf;
-  if (want & 1) CUDA_TRY(cudaMemsetAsync(J, 0, sizeof(double) * mat, st));
-  if (want & 2) CUDA_TRY(cudaMemsetAsync(K, 0, sizeof(double) * mat, st));
-  CUDA_TRY(erik_launch_dmax(D, nD, p->nbf, p->nshell, p->d_sh_bf0, p->d_sh_n, p->d_Dmax, st));
-  CUDA_TRY(cudaMemsetAsync(p->d_counters, 0, sizeof(unsigned long long) * 256, st));
-  CUDA_TRY(cudaMemsetAsync(p->d_stats, 0, sizeof(unsigned long long) * 2 * 256, st));
-  int li = 0;
-  for (const L& l : launches) {
-    KernelArgs a = base_args(p, l.X, l.Y);
-    a.pairs = p->d_pairs;
-    a.bra0 = p->type_off[l.X];
-    a.nbra = p->type_cnt[l.X];
-    a.ket0 = p->type_off[l.Y];
-    a.nket = p->type_cnt[l.Y];
-    a.tri = (l.X == l.Y);
-    a.ntask = l.nt;
-    a.Dmax = p->d_Dmax;
-    a.tau = p->opts.screen_thresh;
-    a.D = D;
-    a.J = J;
-    a.K = K;
-    a.nD = nD;
-    a.want = want;
-    a.mode = KMODE_JK;
-    a.counter = p->d_counters + li;
-    a.scratch = scratch;
-    a.stats = p->d_stats + 2 * (l.X * ERI_NPAIRTYPE + l.Y);
-    CUDA_TRY(erik_launch_class(l.ts, &a, l.grid, l.smem, st));
-    ++li;
-  }
-  if (want & 1) CUDA_TRY(erik_launch_symmetrize(J, nD, p->nbf, st));
-  if (want & 2) CUDA_TRY(erik_launch_symmetrize(K, nD, p->nbf, st));
-  return ERI_OK;
+  std::vector<Launch> launches;
+  if ((s = plan_launches(p, scratch_doubles, &launches)) != ERI_OK) return s;
+  return run_jk(p, launches, D, nD, J, K, flags & 3, (cudaStream_t)cuda_stream, scratch, false, false);
 }

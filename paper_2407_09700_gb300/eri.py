@@ -46,14 +46,16 @@ class eri_stats(ctypes.Structure):
     _fields_ = [("quartets_candidate", ctypes.c_longlong), ("quartets_computed", ctypes.c_longlong),
                 ("prim_quartets", ctypes.c_longlong), ("quartets_fp32", ctypes.c_longlong),
                 ("model_flops", ctypes.c_double), ("npairs_total", ctypes.c_int),
-                ("npairs_kept", ctypes.c_int), ("nclasses_launched", ctypes.c_int)]
+                ("npairs_kept", ctypes.c_int), ("nclasses_launched", ctypes.c_int),
+                ("model_flops_fp32", ctypes.c_double)]
 
 
 class eri_launch_record(ctypes.Structure):
     _fields_ = [("la", ctypes.c_int), ("lb", ctypes.c_int), ("lc", ctypes.c_int), ("ld", ctypes.c_int),
                 ("team_size", ctypes.c_int), ("grid", ctypes.c_int), ("ms", ctypes.c_float),
                 ("quartets", ctypes.c_longlong), ("prim_quartets", ctypes.c_longlong),
-                ("model_flops", ctypes.c_double)]
+                ("model_flops", ctypes.c_double), ("model_flops_fp32", ctypes.c_double), ("fp32", ctypes.c_int),
+                ("specialised", ctypes.c_int)]
 
 
 _lib = None

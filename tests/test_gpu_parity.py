@@ -156,3 +156,61 @@ def test_jk_high_l_reduced():
     Jr, Kr, _ = oracle.jk(m)
     assert np.abs(J - Jr).max() <= 1e-10, np.abs(J - Jr).max()
     assert np.abs(K - Kr).max() <= 1e-10, np.abs(K - Kr).max()
+
+
+# ---------------------------------------------------------------- mixed precision (FP32 recurrences)
+
+def _expected_split(m, Q, tau, thr):
+    """Unique shell quartets passing the screen, split by the mixed-precision bound
+    Q_ij * Q_kl * max|D| (six cross blocks), evaluated in the kernel's order of operations."""
+    f0 = m.shell_first_bf()
+    ns = m.nshell
+    nf = [(int(l) + 1) * (int(l) + 2) // 2 for l in m.shell_l]
+    Dmax = np.zeros((ns, ns))
+    for i in range(ns):
+        for j in range(ns):
+            Dmax[i, j] = np.abs(m.D[:, f0[i]:f0[i] + nf[i], f0[j]:f0[j] + nf[j]]).max()
+    pairs = [(i, j) for i in range(ns) for j in range(i + 1) if Q[i, j] > tau]
+    n64 = n32 = 0
+    for a in range(len(pairs)):
+        P, Qs = pairs[a]
+        for b in range(a + 1):
+            R, S = pairs[b]
+            dm = max(max(Dmax[P, Qs], Dmax[R, S]), max(max(Dmax[P, R], Dmax[P, S]), max(Dmax[Qs, R], Dmax[Qs, S])))
+            bound = Q[P, Qs] * Q[R, S] * dm
+            if bound >= tau:
+                if bound > thr:
+                    n64 += 1
+                else:
+                    n32 += 1
+    return n64, n32
+
+
+@pytest.mark.parametrize("make", [lambda: config_medium(seed=5, natm=4), lambda: _mixed_molecule(seed=3, spread=4.0),
+                                  lambda: config_high_l(seed=6, natm=2, nocc=20)])
+def test_jk_mixed_precision_within_1e6(make):
+    m = make()
+    plan = pkg.Plan(m, precision=pkg.ERI_MIXED, mixed_thresh=1e-4)
+    J, K = _jk_gpu(plan, m.D)
+    Jr, Kr, n = oracle.jk(m)
+    st = plan.stats()
+    n64, n32 = _expected_split(m, plan.schwarz(), m.tau, 1e-4)
+    assert st["quartets_computed"] == n64 + n32
+    assert st["quartets_fp32"] == n32
+    dj, dk = np.abs(J - Jr).max(), np.abs(K - Kr).max()
+    assert dj <= 1e-6 and dk <= 1e-6, (dj, dk)
+
+
+def test_mixed_threshold_extremes():
+    m = config_tiny(seed=1)
+    Jr, Kr, n = oracle.jk(m)
+    # threshold 0: every kept quartet has bound > 0, so everything runs in FP64
+    p0 = pkg.Plan(m, precision=pkg.ERI_MIXED, mixed_thresh=0.0)
+    J, K = _jk_gpu(p0, m.D)
+    assert p0.stats()["quartets_fp32"] == 0
+    assert np.abs(J - Jr).max() <= 1e-10 and np.abs(K - Kr).max() <= 1e-10
+    # threshold huge: everything runs in FP32; still close to the FP64 result
+    p1 = pkg.Plan(m, precision=pkg.ERI_MIXED, mixed_thresh=1e30)
+    J, K = _jk_gpu(p1, m.D)
+    assert p1.stats()["quartets_fp32"] == n
+    assert np.abs(J - Jr).max() <= 1e-5 and np.abs(K - Kr).max() <= 1e-5
