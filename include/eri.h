@@ -61,8 +61,9 @@ typedef struct {
   double screen_thresh;      /* tau of Eqs. 6-9 (Sec. 3); shell pairs with Q <= tau are dropped */
   int precision;             /* ERI_FP64 (all FP64) or ERI_MIXED */
   double mixed_thresh;       /* ERI_MIXED: a quartet whose bound Q_ij Q_kl max|D| (Eqs. 7-9) is <= this
-                                runs its recurrences, Eq. 1 products, contraction and transfer in FP32;
-                                Rys roots/weights, T, digestion and J/K accumulation stay FP64 */
+                                runs its recurrences, Eq. 1 products and contraction in FP32; Rys
+                                roots/weights, T, the transfer relations, digestion and J/K
+                                accumulation stay FP64 */
   int max_nd;                /* largest nD an eri_jk call may pass (>= 1) */
 } eri_opts;
 
@@ -181,6 +182,39 @@ eri_status eri_set_profiling(eri_plan* plan, int enable);
 /* Records of the last eri_jk call (synchronises its stream): writes up to cap records to
  * out (HOST) and the number available to *n.  Requires profiling to have been on. */
 eri_status eri_launch_records(eri_plan* plan, eri_launch_record* out, int cap, int* n);
+
+/*
+ * Batched J/K over several jobs (the serving pattern): every job is (plan, D, J, K,
+ * flags) exactly as for eri_jk, and the result of each job is that of eri_jk on it
+ * alone (up to the order of FP64 atomic additions).  For every angular-momentum
+ * class present in any job, the jobs' screened quartets are compacted into one merged
+ * task list whose entries carry the job index, and the class runs as ONE kernel launch
+ * per precision over all jobs.  Plans may mix ERI_FP64 and ERI_MIXED; all must belong to
+ * the device current when the batch was created.  D, J, K: device pointers per job.
+ * The batch object owns the merged lists and scratch (grown on demand); calls on one
+ * batch must not overlap on the GPU.  Asynchronous on cuda_stream.
+ */
+typedef struct eri_batch eri_batch;
+eri_status eri_batch_create(eri_batch** out);
+eri_status eri_batch_destroy(eri_batch* batch);
+eri_status eri_jk_batch(eri_batch* batch, int njobs, eri_plan* const* plans, const double* const* D,
+                        const int* nD, double* const* J, double* const* K, const int* flags,
+                        void* cuda_stream);
+/* Quartets evaluated by the last eri_jk_batch call (and how many in FP32), class launches. */
+eri_status eri_batch_stats(eri_batch* batch, long long* quartets, long long* quartets_fp32,
+                           int* launches);
+
+/*
+ * One-electron integrals for the RHF driver (the paper evaluates them on the CPU,
+ * Sec. 4): overlap S_ab, kinetic T_ab = -1/2 <a|nabla^2|b> and nuclear attraction
+ * V_ab = -sum_C Z_C <a| 1/|r - R_C| |b> over ncharge point charges (charge_xyz
+ * [ncharge][3] Bohr, charges [ncharge]).  Same shells, normalisation and Cartesian
+ * order as the ERIs.  HOST arrays; S, T, V are [nbf][nbf] row-major, symmetric; any of
+ * them may be NULL.  Needs no GPU.  Errors: ERI_ERR_ARG, ERI_ERR_BASIS,
+ * ERI_ERR_UNSUPPORTED_L.
+ */
+eri_status eri_one_electron(const eri_basis* basis, int ncharge, const double* charge_xyz,
+                            const double* charges, double* S, double* T, double* V);
 
 /* Counters of the last eri_jk call (synchronises that call's stream). */
 eri_status eri_flop_stats(eri_plan* plan, eri_stats* out);

@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liberi.so")
-SOURCES = ["eri_kernels.cu", "eri_small.cu", "eri_plan.cpp", "rys_table.cpp", "eri_noalloc.cu"]
+SOURCES = ["eri_kernels.cu", "eri_small.cu", "eri_plan.cpp", "rys_table.cpp", "eri_noalloc.cu", "eri_onee.cpp"]
 HEADERS = ["eri_internal.h", "rys_table.h", "eri_device.cuh", os.path.join("..", "..", "include", "eri.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -44,6 +44,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
         cmd = [cc, *common, *ARCH, "-c", os.path.join(CSRC, src), "-o", obj]
         if src.endswith(".cu"):
             cmd += ["-Xptxas", "-warn-spills"]
+        else:
+            cmd += ["-Xcompiler", "-fopenmp"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
@@ -54,7 +56,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with concurrent.futures.ThreadPoolExecutor(len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs]
+    cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-lgomp"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -181,16 +181,72 @@ __device__ __forceinline__ int warp_max(int v) { return __reduce_max_sync(0xffff
 // ------------------------------------------------------------------ task decoding and screening
 // Task t of a class enumerates (bra pair, ket pair): rectangular bra x ket, or the
 // triangle ket <= bra when both come from the same pair type.
-__device__ __forceinline__ void decode_task(const KernelArgs& a, long long task, int& ib, int& ik) {
-  if (a.tri) {
+__device__ __forceinline__ void decode_task_in(long long task, bool tri, int bra0, int ket0, int nket, int& ib,
+                                               int& ik) {
+  if (tri) {
     long long i = (long long)((sqrt(8.0 * (double)task + 1.0) - 1.0) * 0.5);
     while (i * (i + 1) / 2 > task) --i;
     while ((i + 1) * (i + 2) / 2 <= task) ++i;
-    ib = a.bra0 + (int)i;
-    ik = a.ket0 + (int)(task - i * (i + 1) / 2);
+    ib = bra0 + (int)i;
+    ik = ket0 + (int)(task - i * (i + 1) / 2);
   } else {
-    ib = a.bra0 + (int)(task / a.nket);
-    ik = a.ket0 + (int)(task % a.nket);
+    ib = bra0 + (int)(task / nket);
+    ik = ket0 + (int)(task % nket);
+  }
+}
+
+__device__ __forceinline__ void decode_task(const KernelArgs& a, long long task, int& ib, int& ik) {
+  decode_task_in(task, a.tri != 0, a.bra0, a.ket0, a.nket, ib, ik);
+}
+
+// What one task reads and writes: the launch's single job, or one job of a batched launch.
+struct TaskCtx {
+  const ShellPair* pairs;
+  const PrimPair* prims;
+  const PrimPairF* primsf;
+  const double* D;
+  double* J;
+  double* K;
+  int nbf, nD, want;
+};
+
+__device__ __forceinline__ TaskCtx single_ctx(const KernelArgs& a) {
+  TaskCtx c;
+  c.pairs = a.pairs;
+  c.prims = a.prims;
+  c.primsf = a.primsf;
+  c.D = a.D;
+  c.J = a.J;
+  c.K = a.K;
+  c.nbf = a.nbf;
+  c.nD = a.nD;
+  c.want = a.want;
+  return c;
+}
+
+// Resolve list position `task` of a JK launch into (bra pair, ket pair) and its job context.
+__device__ __forceinline__ void resolve_task(const KernelArgs& a, long long task, bool listed, TaskCtx& ctx, int& ib,
+                                             int& ik) {
+  if (a.jobs != nullptr) {
+    const unsigned long long e =
+        a.from_back ? a.blist[a.list_cap - 1 - (unsigned long long)task] : a.blist[task];
+    const JobDesc& jd = a.jobs[e >> 32];
+    ctx.pairs = jd.pairs;
+    ctx.prims = jd.prims;
+    ctx.primsf = jd.primsf;
+    ctx.D = jd.D;
+    ctx.J = jd.J;
+    ctx.K = jd.K;
+    ctx.nbf = jd.nbf;
+    ctx.nD = jd.nD;
+    ctx.want = jd.want;
+    decode_task_in((long long)(e & 0xffffffffULL), a.X == a.Y, jd.type_off[a.X], jd.type_off[a.Y],
+                   jd.type_cnt[a.Y], ib, ik);
+  } else if (listed) {
+    const unsigned t = a.from_back ? a.tlist[a.list_cap - 1 - (unsigned long long)task] : a.tlist[task];
+    decode_task(a, (long long)t, ib, ik);
+  } else {
+    decode_task(a, task, ib, ik);
   }
 }
 
@@ -220,10 +276,10 @@ __device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
 // the block (KMODE_BLOCK) or the diagonal maximum (KMODE_SCHWARZ).  Team-cooperative;
 // every lane of the warp calls it.
 template <int TS, typename R>
-__device__ __forceinline__ void finish_quartet(const KernelArgs& a, const ClassDesc& c, R* E0, R* bufA, R* bufB,
-                                               int tl, bool active, const double* AB, const double* CD,
-                                               const ShellPair* bra, const ShellPair* ket, int ib, int ik,
-                                               long long task) {
+__device__ __forceinline__ void finish_quartet(const KernelArgs& a, const TaskCtx& tc, const ClassDesc& c, R* E0,
+                                               R* bufA, R* bufB, int tl, bool active, const double* AB,
+                                               const double* CD, const ShellPair* bra, const ShellPair* ket, int ib,
+                                               int ik, long long task) {
   // ---- 2. transfer relations: bra on e (vector over f), then ket on f (vector over ab)
   const int nab = c.na * c.nb, ncd = c.nc * c.nd;
   const R* Y = hrr_team<R>(c.la, c.lb, AB, c.nf, E0, c.nf, 1, bufA, bufB, tl, TS, active);
@@ -241,11 +297,11 @@ __device__ __forceinline__ void finish_quartet(const KernelArgs& a, const ClassD
       if (ib == ik) w *= 0.5;
       const int p0 = bra->bf0, q0b = bra->bf1, r0 = ket->bf0, s0 = ket->bf1;
       const int na = c.na, nb = c.nb, nc = c.nc, nd = c.nd;
-      const int nbf = a.nbf;
-      for (int xd = 0; xd < a.nD; ++xd) {
-        const double* Dx = a.D + (size_t)xd * nbf * nbf;
-        if (a.want & 1) {
-          double* Jx = a.J + (size_t)xd * nbf * nbf;
+      const int nbf = tc.nbf;
+      for (int xd = 0; xd < tc.nD; ++xd) {
+        const double* Dx = tc.D + (size_t)xd * nbf * nbf;
+        if (tc.want & 1) {
+          double* Jx = tc.J + (size_t)xd * nbf * nbf;
           for (int t = tl; t < nab; t += TS) {
             const int ia = t / nb, ibb = t - (t / nb) * nb;
             double s = 0.0;
@@ -265,8 +321,8 @@ __device__ __forceinline__ void finish_quartet(const KernelArgs& a, const ClassD
             atomicAdd(Jx + (size_t)(r0 + ic) * nbf + s0 + id, 2.0 * w * s);
           }
         }
-        if (a.want & 2) {
-          double* Kx = a.K + (size_t)xd * nbf * nbf;
+        if (tc.want & 2) {
+          double* Kx = tc.K + (size_t)xd * nbf * nbf;
           // K_ac += w sum_bd g D_bd
           for (int t = tl; t < na * nc; t += TS) {
             const int ia = t / nc, ic = t - (t / nc) * nc;

@@ -61,6 +61,20 @@ struct ClassDesc {
 
 enum { KMODE_JK = 0, KMODE_BLOCK = 1, KMODE_SCHWARZ = 2 };
 
+// One job of a batched J/K launch: everything the class kernel reads or writes that
+// belongs to one plan and one density set.
+struct JobDesc {
+  const struct ShellPair* pairs;
+  const struct PrimPair* prims;
+  const struct PrimPairF* primsf;
+  const double* D;
+  double* J;
+  double* K;
+  int nbf, nD, want, pad;
+  int type_off[ERI_NPAIRTYPE];
+  int type_cnt[ERI_NPAIRTYPE];
+};
+
 struct KernelArgs {
   ClassDesc c;
   const ShellPair* pairs;
@@ -81,6 +95,11 @@ struct KernelArgs {
   const unsigned long long* tcount;
   unsigned long long list_cap;
   int from_back;
+  // batched launches (several jobs, one class): entries job << 32 | task of that job,
+  // blist[0 .. *tcount) or from the back as above; X, Y = the class's pair types
+  const JobDesc* jobs;
+  const unsigned long long* blist;
+  int X, Y;
   // densities and outputs (KMODE_JK): row-major [nD][nbf][nbf]
   const double* D;
   double* J;
@@ -114,6 +133,9 @@ int erik_blocks_per_sm(int ts, int fp32, int smem_bytes, int* out);
 int erik_launch_class(int ts, int fp32, const struct KernelArgs* a, int grid, int smem_bytes, void* stream);
 int erik_launch_compact(const struct KernelArgs* a, unsigned* tlist, unsigned long long cap,
                         unsigned long long* counts, unsigned* tiles, int mixed, void* stream);
+int erik_launch_compact_batched(const struct KernelArgs* a, unsigned long long* blist, unsigned long long cap,
+                                unsigned long long* counts, unsigned* tiles, unsigned long long* cursor,
+                                unsigned long long* base, unsigned long long job, int mixed, void* stream);
 int erik_launch_dmax(const double* D, int nD, int nbf, int nsh, const int* sh_bf0, const int* sh_n,
                      double* Dmax, void* stream);
 int erik_launch_symmetrize(double* M, int nD, int nbf, void* stream);

@@ -132,11 +132,51 @@ __global__ void compact_write_kernel(const KernelArgs a, int mixed, const unsign
   }
 }
 
+// Batched variant: reserve this job's place in a class's merged lists, then write
+// entries job << 32 | task (FP64 list from the front, FP32 list from the back).
+__global__ void compact_reserve_kernel(const unsigned long long* counts, unsigned long long* cursor,
+                                       unsigned long long* base) {
+  if (threadIdx.x == 0) {
+    base[0] = atomicAdd(cursor + 0, counts[0]);
+    base[1] = atomicAdd(cursor + 1, counts[1]);
+  }
+}
+
+__global__ void compact_write_batched_kernel(const KernelArgs a, int mixed, const unsigned* tileoff,
+                                             unsigned long long* blist, unsigned long long cap,
+                                             unsigned long long job, const unsigned long long* base) {
+  __shared__ unsigned s1[8], s2[8];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const long long t0 = (long long)blockIdx.x * CTILE;
+  unsigned long long base1 = base[0] + tileoff[2 * blockIdx.x], base2 = base[1] + tileoff[2 * blockIdx.x + 1];
+  for (int k = 0; k < CTILE / 256; ++k) {
+    const long long task = t0 + k * 256 + threadIdx.x;
+    const int cat = task_category(a, task, mixed);
+    const unsigned m1 = __ballot_sync(0xffffffffu, cat == 1), m2 = __ballot_sync(0xffffffffu, cat == 2);
+    if (lane == 0) { s1[wid] = __popc(m1); s2[wid] = __popc(m2); }
+    __syncthreads();
+    unsigned long long p1 = base1, p2 = base2;
+    unsigned tot1 = 0, tot2 = 0;
+    for (int w = 0; w < 8; ++w) {
+      if (w < wid) { p1 += s1[w]; p2 += s2[w]; }
+      tot1 += s1[w];
+      tot2 += s2[w];
+    }
+    const unsigned below = (1u << lane) - 1u;
+    const unsigned long long e = (job << 32) | (unsigned long long)(unsigned)task;
+    if (cat == 1) blist[p1 + __popc(m1 & below)] = e;
+    if (cat == 2) blist[cap - 1 - (p2 + __popc(m2 & below))] = e;
+    base1 += tot1;
+    base2 += tot2;
+    __syncthreads();
+  }
+}
+
 // ------------------------------------------------------------------ the class kernel
 // R = double: the FP64 path.  R = float: the FP32 path of the mixed mode (Sec. 2's
-// recurrences, Eq. 1's products, the Eq. 5 contraction and the transfer relations in
-// FP32; T and the Rys roots / weights in FP64, rounded at the recurrence input;
-// digestion and the J / K accumulation in FP64).
+// recurrences, Eq. 1's products and the Eq. 5 contraction in FP32; T and the Rys roots /
+// weights in FP64, rounded at the recurrence input; the transfer relations, digestion and
+// the J / K accumulation in FP64).
 template <int TS, typename R>
 __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : 2)) eri_class_kernel(const KernelArgs a) {
   extern __shared__ double smem[];
@@ -165,15 +205,16 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : 2)) eri_class_kernel(const
     sr.es = 1;
   }
   const int S_2D = bp * NPR;                         // R offset of the 2D tables
-  R* scr = reinterpret_cast<R*>(a.scratch + gteam * c.scratch_per_team);
-  R* E0 = scr;                                       // [ne][nf] contracted [e0|f0]
-  R* bufA = scr + c.nout;
-  R* bufB = bufA + c.hrr_doubles;
-  const PP* prims_r = reinterpret_cast<const PP*>(sizeof(R) == 8 ? (const void*)a.prims : (const void*)a.primsf);
+  // contracted [e0|f0] and the transfer relations are FP64 in both paths: the FP32 path
+  // hands its contracted values over before the transfer, whose cancellations grow with |A-B|
+  double* scr = a.scratch + gteam * c.scratch_per_team;
+  double* E0 = scr;                                  // [ne][nf] contracted [e0|f0]
+  double* bufA = scr + c.nout;
+  double* bufB = bufA + c.hrr_doubles;
 
   unsigned long long cnt_q = 0, cnt_p = 0;
 
-  const bool listed = (a.mode == KMODE_JK) && (a.tlist != nullptr);
+  const bool listed = (a.mode == KMODE_JK) && (a.tlist != nullptr || a.jobs != nullptr);
   const long long ntask = listed ? (long long)*a.tcount : a.ntask;
 
   while (true) {
@@ -187,19 +228,18 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : 2)) eri_class_kernel(const
 
     // ---- decode the task into (bra pair, ket pair)
     int ib = 0, ik = 0;
+    TaskCtx tc = single_ctx(a);
     if (active) {
       if (a.mode != KMODE_JK) {
         ib = a.tasklist[2 * task];
         ik = a.tasklist[2 * task + 1];
-      } else if (listed) {
-        const unsigned t = a.from_back ? a.tlist[a.list_cap - 1 - (unsigned long long)task] : a.tlist[task];
-        decode_task(a, (long long)t, ib, ik);
       } else {
-        decode_task(a, task, ib, ik);
+        resolve_task(a, task, listed, tc, ib, ik);
       }
     }
-    const ShellPair* bra = a.pairs + ib;
-    const ShellPair* ket = a.pairs + ik;
+    const PP* prims_r = reinterpret_cast<const PP*>(sizeof(R) == 8 ? (const void*)tc.prims : (const void*)tc.primsf);
+    const ShellPair* bra = tc.pairs + ib;
+    const ShellPair* ket = tc.pairs + ik;
     // ---- screening (Eqs. 7-9): Q_ij Q_kl max|D| over the six cross blocks >= tau;
     //      in the mixed mode the same bound picks the precision (FP64 above mixed_thr).
     //      Listed tasks were screened by compact_kernel.
@@ -243,8 +283,8 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : 2)) eri_class_kernel(const
           if (j < nbt) {
             const int q = q0 + j;
             const int ixp = boff + q / npk, iyp = koff + q % npk;
-            const PrimPair* xd = a.prims + ixp;
-            const PrimPair* yd = a.prims + iyp;
+            const PrimPair* xd = tc.prims + ixp;
+            const PrimPair* yd = tc.prims + iyp;
             const double s = xd->zeta + yd->zeta;
             const double rd = rsqrt(s);
             const double PQ0 = xd->P[0] - yd->P[0], PQ1 = xd->P[1] - yd->P[1], PQ2 = xd->P[2] - yd->P[2];
@@ -333,13 +373,13 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : 2)) eri_class_kernel(const
 #pragma unroll
         for (int k = 0; k < GSLOTS; ++k) {
           const int o = o0 + k * TS + tl;
-          if (k < kcnt && o < c.nout) E0[o] = acc[k];
+          if (k < kcnt && o < c.nout) E0[o] = (double)acc[k];
         }
       }
     }
     __syncwarp();
 
-    finish_quartet<TS, R>(a, c, E0, bufA, bufB, tl, active, AB, CD, bra, ket, ib, ik, task);
+    finish_quartet<TS, double>(a, tc, c, E0, bufA, bufB, tl, active, AB, CD, bra, ket, ib, ik, task);
     __syncwarp();
   }
   // ---- counters: one atomic pair per warp
@@ -485,6 +525,19 @@ extern "C" int erik_launch_compact(const KernelArgs* a, unsigned* tlist, unsigne
   compact_count_kernel<<<(unsigned)ntiles, 256, 0, st>>>(*a, mixed, tiles);
   compact_scan_kernel<<<1, 1024, 0, st>>>(tiles, ntiles, counts);
   compact_write_kernel<<<(unsigned)ntiles, 256, 0, st>>>(*a, mixed, tiles, tlist, cap);
+  return (int)cudaGetLastError();
+}
+
+extern "C" int erik_launch_compact_batched(const KernelArgs* a, unsigned long long* blist, unsigned long long cap,
+                                           unsigned long long* counts, unsigned* tiles, unsigned long long* cursor,
+                                           unsigned long long* base, unsigned long long job, int mixed, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long ntiles = (a->ntask + CTILE - 1) / CTILE;
+  if (ntiles == 0) return (int)cudaSuccess;
+  compact_count_kernel<<<(unsigned)ntiles, 256, 0, st>>>(*a, mixed, tiles);
+  compact_scan_kernel<<<1, 1024, 0, st>>>(tiles, ntiles, counts);
+  compact_reserve_kernel<<<1, 32, 0, st>>>(counts, cursor, base);
+  compact_write_batched_kernel<<<(unsigned)ntiles, 256, 0, st>>>(*a, mixed, tiles, blist, cap, job, base);
   return (int)cudaGetLastError();
 }
 

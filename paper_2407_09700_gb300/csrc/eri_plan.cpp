@@ -189,8 +189,8 @@ eri_status device_init(int dev, DeviceState** out) {
 // eri_kernels.cu, split by pipe: per primitive quartet the Gaussian-product scalars and T,
 // per root the two degree-11 Horner sums (FP64 always) and the recurrence coefficients,
 // the three 2D tables and the Eq. 1 products (a multiply and an FMA per [e0|f0] value and
-// root); per contracted quartet the transfer relations and the six digestion updates (FP64
-// always).  fp32 = 1 counts the FP32 path of the mixed mode.
+// root); per contracted quartet the transfer relations and the six digestion updates (both
+// FP64 always).  fp32 = 1 counts the FP32 path of the mixed mode.
 void class_model_flops2(const ClassDesc& c, int nD, int want, int fp32, double* prim64, double* prim32,
                         double* quart64, double* quart32) {
   const int N = c.nroots, Le = c.Le, Lf = c.Lf;
@@ -220,8 +220,8 @@ void class_model_flops2(const ClassDesc& c, int nD, int want, int fp32, double* 
   if (fp32) {
     *prim64 = t_setup + N * horner;
     *prim32 = r_setup + 4 + rec;                       // + FP32 rsqrt and PQ
-    *quart64 = dig;
-    *quart32 = hrr;
+    *quart64 = hrr + dig;
+    *quart32 = 0.0;
   } else {
     *prim64 = t_setup + r_setup + N * horner + rec;
     *prim32 = 0.0;
@@ -984,7 +984,17 @@ eri_status eri_probe_fma_peak(double* fp64_tflops, double* fp32_tflops) {
 
 }  // extern "C"
 
-// ================================================================= internal hooks for eri_noalloc.cu
+// ================================================================= internal hooks for other translation units
+extern "C" __attribute__((visibility("hidden"))) void eri_host_normalise(int nshell, const int* l, const int* nprim,
+                                                                          const int* off, const double* exps,
+                                                                          const double* raw, double* out) {
+  int n = 0;
+  for (int s = 0; s < nshell; ++s) n = std::max(n, off[s] + nprim[s]);
+  std::vector<double> tmp(raw, raw + n);
+  normalise(nshell, l, nprim, off, exps, raw, tmp);
+  std::copy(tmp.begin(), tmp.end(), out);
+}
+
 // Record a failure for eri_last_error() from another translation unit.
 extern "C" __attribute__((visibility("hidden"))) eri_status eri_internal_fail(eri_status s, const char* msg) {
   return fail(s, "%s", msg);
@@ -1007,3 +1017,232 @@ extern "C" __attribute__((visibility("hidden"))) eri_status eri_internal_jk_fixe
   if ((s = plan_launches(p, scratch_doubles, &launches)) != ERI_OK) return s;
   return run_jk(p, launches, D, nD, J, K, flags & 3, (cudaStream_t)cuda_stream, scratch, false, false);
 }
+
+// ================================================================= batched J/K across plans
+struct eri_batch {
+  int device = 0;
+  JobDesc* d_jobs = nullptr;
+  size_t jobs_cap = 0;
+  unsigned long long* d_blist = nullptr;
+  size_t blist_cap = 0;
+  unsigned* d_tiles = nullptr;
+  size_t tiles_cap = 0;
+  unsigned long long* d_small = nullptr;     // counts[2], base[2]
+  unsigned long long* d_cursor = nullptr;    // [256][2]
+  unsigned long long* d_counter = nullptr;   // [512]
+  unsigned long long* d_stats = nullptr;     // [2][256][2]
+  double* d_scratch = nullptr;
+  size_t scratch_doubles = 0;
+  cudaStream_t last_stream = nullptr;
+  long long last_quartets = 0;
+  int last_launches = 0;
+};
+
+extern "C" {
+
+eri_status eri_batch_create(eri_batch** out) {
+  g_err.clear();
+  if (!out) return fail(ERI_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+    cudaGetLastError();
+    return fail(ERI_ERR_NO_DEVICE, "no CUDA device is visible");
+  }
+  eri_batch* b = new (std::nothrow) eri_batch();
+  if (!b) return fail(ERI_ERR_OOM, "host allocation failed");
+  cudaGetDevice(&b->device);
+  if (cudaMalloc(&b->d_small, sizeof(unsigned long long) * 4) != cudaSuccess ||
+      cudaMalloc(&b->d_cursor, sizeof(unsigned long long) * 2 * 256) != cudaSuccess ||
+      cudaMalloc(&b->d_counter, sizeof(unsigned long long) * 512) != cudaSuccess ||
+      cudaMalloc(&b->d_stats, sizeof(unsigned long long) * 4 * 256) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(b->d_small); cudaFree(b->d_cursor); cudaFree(b->d_counter); cudaFree(b->d_stats);
+    delete b;
+    return fail(ERI_ERR_OOM, "device allocation failed in eri_batch_create");
+  }
+  *out = b;
+  return ERI_OK;
+}
+
+eri_status eri_batch_destroy(eri_batch* b) {
+  if (!b) return ERI_OK;
+  cudaSetDevice(b->device);
+  cudaDeviceSynchronize();
+  void* bufs[] = {b->d_jobs, b->d_blist, b->d_tiles, b->d_small, b->d_cursor, b->d_counter, b->d_stats, b->d_scratch};
+  for (void* x : bufs)
+    if (x) cudaFree(x);
+  delete b;
+  return ERI_OK;
+}
+
+eri_status eri_jk_batch(eri_batch* b, int njobs, eri_plan* const* plans, const double* const* D, const int* nD,
+                        double* const* J, double* const* K, const int* flags, void* cuda_stream) {
+  g_err.clear();
+  if (!b || njobs < 1 || !plans || !D || !nD || !J || !K || !flags) return fail(ERI_ERR_ARG, "NULL argument or njobs < 1");
+  if (njobs > (1 << 24)) return fail(ERI_ERR_ARG, "too many jobs");
+  eri_status s;
+  for (int j = 0; j < njobs; ++j) {
+    if ((s = check_jk_args(plans[j], D[j], nD[j], J[j], K[j], flags[j])) != ERI_OK) return s;
+    if (plans[j]->device != b->device) return fail(ERI_ERR_ARG, "job %d's plan is on another device", j);
+  }
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  eri_plan* p0 = plans[0];
+  // ---- job descriptors
+  std::vector<JobDesc> jobs(njobs);
+  bool any_mixed = false;
+  for (int j = 0; j < njobs; ++j) {
+    eri_plan* p = plans[j];
+    JobDesc& jd = jobs[j];
+    memset(&jd, 0, sizeof(jd));
+    jd.pairs = p->d_pairs;
+    jd.prims = p->d_prims;
+    jd.primsf = p->d_primsf;
+    jd.D = D[j];
+    jd.J = J[j];
+    jd.K = K[j];
+    jd.nbf = p->nbf;
+    jd.nD = nD[j];
+    jd.want = flags[j] & 3;
+    for (int t = 0; t < ERI_NPAIRTYPE; ++t) {
+      jd.type_off[t] = p->type_off[t];
+      jd.type_cnt[t] = p->type_cnt[t];
+    }
+    any_mixed = any_mixed || p->opts.precision == ERI_MIXED;
+  }
+  if ((s = ensure_buf(&b->d_jobs, &b->jobs_cap, (size_t)njobs)) != ERI_OK) return s;
+  CUDA_TRY(cudaMemcpyAsync(b->d_jobs, jobs.data(), sizeof(JobDesc) * njobs, cudaMemcpyHostToDevice, st));
+  // ---- classes present in any job, their merged capacities and launch shapes
+  struct BL { int X, Y; long long total; long long maxnt; };
+  std::vector<BL> cls;
+  for (int X = 0; X < ERI_NPAIRTYPE; ++X)
+    for (int Y = 0; Y <= X; ++Y) {
+      long long tot = 0, mx = 0;
+      for (int j = 0; j < njobs; ++j) {
+        const long long nx = plans[j]->type_cnt[X], ny = plans[j]->type_cnt[Y];
+        if (!nx || !ny) continue;
+        const long long nt = (X == Y) ? nx * (nx + 1) / 2 : nx * ny;
+        if ((unsigned long long)nt > 0xffffffffULL) return fail(ERI_ERR_ARG, "job %d has more than 2^32 tasks in a class", j);
+        tot += nt;
+        mx = std::max(mx, nt);
+      }
+      if (tot) cls.push_back({X, Y, tot, mx});
+    }
+  size_t cap = 1, tcap = 2, need = 0;
+  struct LL { int X, Y, fp32, grid, smem, ts, small; long long total; };
+  std::vector<LL> launches;
+  for (const BL& c : cls) {
+    cap = std::max(cap, (size_t)c.total);
+    tcap = std::max(tcap, (size_t)(2 * ((c.maxnt + 1023) / 1024 + 1)));
+    for (int fp32 = 0; fp32 < (any_mixed ? 2 : 1); ++fp32) {
+      LL l{c.X, c.Y, fp32, 0, 0, 0, 0, c.total};
+      if ((s = launch_shape(p0, c.X, c.Y, fp32, c.total, &l.grid, &l.smem, &l.ts)) != ERI_OK) return s;
+      const ClassDesc& cd = p0->dev->classes[c.X][c.Y];
+      if (l.ts == 1 && erik_small_available(cd.la, cd.lb, cd.lc, cd.ld)) {
+        int bps = 0;
+        CUDA_TRY(erik_small_blocks_per_sm(cd.la, cd.lb, cd.lc, cd.ld, fp32, &bps));
+        l.grid = (int)std::max(1LL, std::min((long long)p0->dev->sms * std::max(bps, 1), (c.total + 127) / 128));
+        l.smem = 0;
+        l.small = 1;
+      }
+      need = std::max(need, (size_t)l.grid * (size_t)(128 / l.ts) * (size_t)cd.scratch_per_team);
+      launches.push_back(l);
+    }
+  }
+  if ((s = ensure_buf(&b->d_blist, &b->blist_cap, cap)) != ERI_OK) return s;
+  if ((s = ensure_buf(&b->d_tiles, &b->tiles_cap, tcap)) != ERI_OK) return s;
+  if (need > b->scratch_doubles) {
+    if (b->d_scratch) {
+      CUDA_TRY(cudaDeviceSynchronize());
+      cudaFree(b->d_scratch);
+      b->d_scratch = nullptr;
+      b->scratch_doubles = 0;
+    }
+    CUDA_TRY(cudaMalloc(&b->d_scratch, sizeof(double) * need));
+    b->scratch_doubles = need;
+  }
+  // ---- per job: zero outputs, density block maxima
+  for (int j = 0; j < njobs; ++j) {
+    eri_plan* p = plans[j];
+    const size_t mat = (size_t)nD[j] * p->nbf * p->nbf;
+    if (flags[j] & 1) CUDA_TRY(cudaMemsetAsync(J[j], 0, sizeof(double) * mat, st));
+    if (flags[j] & 2) CUDA_TRY(cudaMemsetAsync(K[j], 0, sizeof(double) * mat, st));
+    CUDA_TRY(erik_launch_dmax(D[j], nD[j], p->nbf, p->nshell, p->d_sh_bf0, p->d_sh_n, p->d_Dmax, st));
+  }
+  CUDA_TRY(cudaMemsetAsync(b->d_cursor, 0, sizeof(unsigned long long) * 2 * 256, st));
+  CUDA_TRY(cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long) * 512, st));
+  CUDA_TRY(cudaMemsetAsync(b->d_stats, 0, sizeof(unsigned long long) * 4 * 256, st));
+  // ---- per class: merged compaction over jobs, then one launch per precision
+  int li = 0;
+  for (size_t ci = 0; ci < cls.size(); ++ci) {
+    const BL& c = cls[ci];
+    unsigned long long* cursor = b->d_cursor + 2 * ci;
+    for (int j = 0; j < njobs; ++j) {
+      eri_plan* p = plans[j];
+      const long long nx = p->type_cnt[c.X], ny = p->type_cnt[c.Y];
+      if (!nx || !ny) continue;
+      KernelArgs a = base_args(p, c.X, c.Y);
+      a.pairs = p->d_pairs;
+      a.bra0 = p->type_off[c.X];
+      a.nbra = (int)nx;
+      a.ket0 = p->type_off[c.Y];
+      a.nket = (int)ny;
+      a.tri = (c.X == c.Y);
+      a.ntask = (c.X == c.Y) ? nx * (nx + 1) / 2 : nx * ny;
+      a.Dmax = p->d_Dmax;
+      a.nsh = p->nshell;
+      a.tau = p->opts.screen_thresh;
+      a.mixed_thr = p->opts.mixed_thresh;
+      CUDA_TRY(erik_launch_compact_batched(&a, b->d_blist, (unsigned long long)c.total, b->d_small, b->d_tiles,
+                                           cursor, b->d_small + 2, (unsigned long long)j,
+                                           p->opts.precision == ERI_MIXED ? 1 : 0, st));
+    }
+    for (const LL& l : launches) {
+      if (l.X != c.X || l.Y != c.Y) continue;
+      KernelArgs a = base_args(p0, c.X, c.Y);
+      a.mode = KMODE_JK;
+      a.jobs = b->d_jobs;
+      a.blist = b->d_blist;
+      a.list_cap = (unsigned long long)c.total;
+      a.from_back = l.fp32;
+      a.tcount = cursor + l.fp32;
+      a.X = c.X;
+      a.Y = c.Y;
+      a.counter = b->d_counter + li;
+      a.scratch = b->d_scratch;
+      a.stats = b->d_stats + 2 * (256 * l.fp32 + c.X * ERI_NPAIRTYPE + c.Y);
+      if (l.small)
+        CUDA_TRY(erik_launch_small(a.c.la, a.c.lb, a.c.lc, a.c.ld, l.fp32, &a, l.grid, st));
+      else
+        CUDA_TRY(erik_launch_class(l.ts, l.fp32, &a, l.grid, l.smem, st));
+      ++li;
+    }
+  }
+  for (int j = 0; j < njobs; ++j) {
+    if (flags[j] & 1) CUDA_TRY(erik_launch_symmetrize(J[j], nD[j], plans[j]->nbf, st));
+    if (flags[j] & 2) CUDA_TRY(erik_launch_symmetrize(K[j], nD[j], plans[j]->nbf, st));
+  }
+  b->last_stream = st;
+  b->last_launches = li;
+  return ERI_OK;
+}
+
+eri_status eri_batch_stats(eri_batch* b, long long* quartets, long long* quartets_fp32, int* launches) {
+  g_err.clear();
+  if (!b) return fail(ERI_ERR_ARG, "batch is NULL");
+  CUDA_TRY(cudaStreamSynchronize(b->last_stream));
+  std::vector<unsigned long long> st(4 * 256);
+  CUDA_TRY(cudaMemcpy(st.data(), b->d_stats, sizeof(unsigned long long) * 4 * 256, cudaMemcpyDeviceToHost));
+  long long q = 0, q32 = 0;
+  for (int f = 0; f < 2; ++f)
+    for (int k = 0; k < 256; ++k) {
+      q += (long long)st[2 * (256 * f + k)];
+      if (f) q32 += (long long)st[2 * (256 * f + k)];
+    }
+  if (quartets) *quartets = q;
+  if (quartets_fp32) *quartets_fp32 = q32;
+  if (launches) *launches = b->last_launches;
+  return ERI_OK;
+}
+
+}  // extern "C"

@@ -56,12 +56,12 @@ __global__ void __launch_bounds__(TPB, 3) eri_small_kernel(const KernelArgs a) {
   const int lane = threadIdx.x & 31;
   const long long gteam = (long long)blockIdx.x * TPB + threadIdx.x;
   const ClassDesc& c = a.c;
-  R* scr = reinterpret_cast<R*>(a.scratch + gteam * c.scratch_per_team);
-  R* E0 = scr;
-  R* bufA = scr + c.nout;
-  R* bufB = bufA + c.hrr_doubles;
-  const PP* prims_r = reinterpret_cast<const PP*>(sizeof(R) == 8 ? (const void*)a.prims : (const void*)a.primsf);
-  const bool listed = a.tlist != nullptr;
+  // contracted [e0|f0] and the transfer relations are FP64 in both paths (see eri_kernels.cu)
+  double* scr = a.scratch + gteam * c.scratch_per_team;
+  double* E0 = scr;
+  double* bufA = scr + c.nout;
+  double* bufB = bufA + c.hrr_doubles;
+  const bool listed = a.tlist != nullptr || a.jobs != nullptr;
   const long long ntask = listed ? (long long)*a.tcount : a.ntask;
   unsigned long long cnt_q = 0, cnt_p = 0;
 
@@ -73,16 +73,11 @@ __global__ void __launch_bounds__(TPB, 3) eri_small_kernel(const KernelArgs a) {
     const long long task = (long long)tbase + lane;
     bool active = task < ntask;
     int ib = 0, ik = 0;
-    if (active) {
-      if (listed) {
-        const unsigned t = a.from_back ? a.tlist[a.list_cap - 1 - (unsigned long long)task] : a.tlist[task];
-        decode_task(a, (long long)t, ib, ik);
-      } else {
-        decode_task(a, task, ib, ik);
-      }
-    }
-    const ShellPair* bra = a.pairs + ib;
-    const ShellPair* ket = a.pairs + ik;
+    TaskCtx tc = single_ctx(a);
+    if (active) resolve_task(a, task, listed, tc, ib, ik);
+    const PP* prims_r = reinterpret_cast<const PP*>(sizeof(R) == 8 ? (const void*)tc.prims : (const void*)tc.primsf);
+    const ShellPair* bra = tc.pairs + ib;
+    const ShellPair* ket = tc.pairs + ik;
     if (active && !listed) {
       const double bound = quartet_bound(a, bra, ket);
       active = bound >= a.tau;
@@ -108,8 +103,8 @@ __global__ void __launch_bounds__(TPB, 3) eri_small_kernel(const KernelArgs a) {
     for (int q = 0; q < maxq; ++q) {
       if (q < nq) {
         const int ixp = boff + q / npk, iyp = koff + q % npk;
-        const PrimPair* xd = a.prims + ixp;
-        const PrimPair* yd = a.prims + iyp;
+        const PrimPair* xd = tc.prims + ixp;
+        const PrimPair* yd = tc.prims + iyp;
         // T and the Rys-table lookup in FP64
         const double s = xd->zeta + yd->zeta;
         const double rd = rsqrt(s);
@@ -194,10 +189,10 @@ __global__ void __launch_bounds__(TPB, 3) eri_small_kernel(const KernelArgs a) {
     }
     if (active) {
 #pragma unroll
-      for (int o = 0; o < NOUT; ++o) E0[o] = acc[o];
+      for (int o = 0; o < NOUT; ++o) E0[o] = (double)acc[o];
     }
     __syncwarp();
-    finish_quartet<1, R>(a, c, E0, bufA, bufB, 0, active, AB, CD, bra, ket, ib, ik, task);
+    finish_quartet<1, double>(a, tc, c, E0, bufA, bufB, 0, active, AB, CD, bra, ket, ib, ik, task);
     __syncwarp();
   }
   for (int off = 16; off > 0; off >>= 1) {

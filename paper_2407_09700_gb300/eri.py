@@ -79,6 +79,15 @@ _SIGS = {
     "eri_set_profiling": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "eri_launch_records": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(eri_launch_record), ctypes.c_int,
                                           ctypes.POINTER(ctypes.c_int)]),
+    "eri_one_electron": (ctypes.c_int, [ctypes.POINTER(eri_basis), ctypes.c_int, _dp, _dp, _dp, _dp, _dp]),
+    "eri_batch_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p)]),
+    "eri_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "eri_jk_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p),
+                                    ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int),
+                                    ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
+                                    ctypes.POINTER(ctypes.c_int), ctypes.c_void_p]),
+    "eri_batch_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong),
+                                       ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_int)]),
     "eri_last_error": (ctypes.c_char_p, []),
 }
 
@@ -130,7 +139,7 @@ def _stream_handle(stream):
 class Plan:
     """An eri_plan built from a molecule-like object (coords, shell_* arrays, exps, coefs)."""
 
-    def __init__(self, mol, tau=None, precision=ERI_FP64, mixed_thresh=1e-4, max_nd=8, normalise=True,
+    def __init__(self, mol, tau=None, precision=ERI_FP64, mixed_thresh=1e-5, max_nd=8, normalise=True,
                  stream=None):
         lib = load_library()
         self._arrs = dict(
@@ -243,3 +252,70 @@ def probe_fma_peak():
     a, b = ctypes.c_double(), ctypes.c_double()
     _check(load_library().eri_probe_fma_peak(ctypes.byref(a), ctypes.byref(b)))
     return a.value, b.value
+
+
+def one_electron(mol, charges=None, charge_xyz=None, normalise=True):
+    """Host one-electron integrals (S, T, V) of a molecule-like object; V uses the
+    molecule's nuclear charges at its atom positions unless charges are given."""
+    lib = load_library()
+    coords = np.ascontiguousarray(mol.coords, dtype=np.float64)
+    arrs = [np.ascontiguousarray(x, dtype=np.int32) for x in (mol.shell_atom, mol.shell_l, mol.shell_nprim,
+                                                             mol.shell_off)]
+    exps = np.ascontiguousarray(mol.exps, dtype=np.float64)
+    coefs = np.ascontiguousarray(mol.coefs, dtype=np.float64)
+    b = eri_basis(coords.shape[0], _d(coords), int(arrs[1].shape[0]), _i(arrs[0]), _i(arrs[1]), _i(arrs[2]),
+                  _i(arrs[3]), _d(exps), _d(coefs), 1 if normalise else 0)
+    if charges is None:
+        charges = mol.charges
+        charge_xyz = coords
+    q = np.ascontiguousarray(charges, dtype=np.float64)
+    qx = np.ascontiguousarray(charge_xyz, dtype=np.float64).reshape(-1, 3)
+    nbf = int(sum((int(l) + 1) * (int(l) + 2) // 2 for l in mol.shell_l))
+    S = np.zeros((nbf, nbf))
+    T = np.zeros((nbf, nbf))
+    V = np.zeros((nbf, nbf))
+    _check(lib.eri_one_electron(ctypes.byref(b), int(q.size), _d(qx), _d(q), _d(S), _d(T), _d(V)))
+    return S, T, V
+
+
+class Batch:
+    """eri_jk_batch: one launch per class (and precision) across several jobs."""
+
+    def __init__(self):
+        h = ctypes.c_void_p()
+        _check(load_library().eri_batch_create(ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load_library().eri_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def jk(self, plans, Ds, Js=None, Ks=None, want=ERI_WANT_J | ERI_WANT_K, stream=None):
+        """Ds: list of CUDA float64 tensors [nD, nbf, nbf] (one per plan).  Returns (Js, Ks)."""
+        import torch
+        n = len(plans)
+        Ds = [D if D.dim() == 3 else D.unsqueeze(0) for D in Ds]
+        if Js is None:
+            Js = [torch.empty_like(D) for D in Ds]
+        if Ks is None:
+            Ks = [torch.empty_like(D) for D in Ds]
+        P = (ctypes.c_void_p * n)(*[p._h.value for p in plans])
+        Dp = (ctypes.c_void_p * n)(*[D.data_ptr() for D in Ds])
+        Jp = (ctypes.c_void_p * n)(*[J.data_ptr() for J in Js])
+        Kp = (ctypes.c_void_p * n)(*[K.data_ptr() for K in Ks])
+        nD = (ctypes.c_int * n)(*[D.shape[0] for D in Ds])
+        fl = (ctypes.c_int * n)(*([want] * n))
+        _check(load_library().eri_jk_batch(self._h, n, P, Dp, nD, Jp, Kp, fl, _stream_handle(stream)))
+        return Js, Ks
+
+    def stats(self):
+        q, q32, nl = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_int()
+        _check(load_library().eri_batch_stats(self._h, ctypes.byref(q), ctypes.byref(q32), ctypes.byref(nl)))
+        return {"quartets": q.value, "quartets_fp32": q32.value, "launches": nl.value}

@@ -190,11 +190,11 @@ def _expected_split(m, Q, tau, thr):
                                   lambda: config_high_l(seed=6, natm=2, nocc=20)])
 def test_jk_mixed_precision_within_1e6(make):
     m = make()
-    plan = pkg.Plan(m, precision=pkg.ERI_MIXED, mixed_thresh=1e-4)
+    plan = pkg.Plan(m, precision=pkg.ERI_MIXED, mixed_thresh=1e-5)
     J, K = _jk_gpu(plan, m.D)
     Jr, Kr, n = oracle.jk(m)
     st = plan.stats()
-    n64, n32 = _expected_split(m, plan.schwarz(), m.tau, 1e-4)
+    n64, n32 = _expected_split(m, plan.schwarz(), m.tau, 1e-5)
     assert st["quartets_computed"] == n64 + n32
     assert st["quartets_fp32"] == n32
     dj, dk = np.abs(J - Jr).max(), np.abs(K - Kr).max()
@@ -214,3 +214,29 @@ def test_mixed_threshold_extremes():
     J, K = _jk_gpu(p1, m.D)
     assert p1.stats()["quartets_fp32"] == n
     assert np.abs(J - Jr).max() <= 1e-5 and np.abs(K - Kr).max() <= 1e-5
+
+
+# ---------------------------------------------------------------- batched launches across jobs
+
+def test_batch_same_alone_and_in_the_mix():
+    mols = [config_tiny(seed=3), _mixed_molecule(seed=5, natm=2, lmax=3), config_medium(seed=7, natm=3),
+            config_high_l(seed=8, natm=2, nocc=20)]
+    precs = [pkg.ERI_FP64, pkg.ERI_MIXED, pkg.ERI_FP64, pkg.ERI_MIXED]
+    plans = [pkg.Plan(m, precision=p) for m, p in zip(mols, precs)]
+    Ds = [torch.from_numpy(np.ascontiguousarray(m.D)).cuda() for m in mols]
+    alone = []
+    for p, D in zip(plans, Ds):
+        J, K = p.jk(D)
+        alone.append((J.clone(), K.clone()))
+    batch = pkg.Batch()
+    for rep in range(2):
+        Js, Ks = batch.jk(plans, Ds)
+        torch.cuda.synchronize()
+        for (Ja, Ka), J, K, prec in zip(alone, Js, Ks, precs):
+            tol = 1e-12 if prec == pkg.ERI_FP64 else 1e-9
+            sj = float(Ja.abs().max())
+            assert float((J - Ja).abs().max()) <= tol * sj
+            assert float((K - Ka).abs().max()) <= tol * float(Ka.abs().max())
+    st = batch.stats()
+    total = sum(p.stats()["quartets_computed"] for p in plans)
+    assert st["quartets"] == total

@@ -45,6 +45,7 @@ class Molecule:
     D: Optional[np.ndarray] = None   # (nD, nbf, nbf) float64 symmetric PSD densities
     tau: float = 1e-12          # Schwarz / density screening threshold
     seed: int = 0
+    net_charge: int = 0         # molecular charge (the SCF recipe sets +1 to make the electron count even)
 
     @property
     def natm(self) -> int:
@@ -71,7 +72,9 @@ class Molecule:
         m.coords = self.coords + np.asarray(shift_bohr, dtype=np.float64)[None, :]
         return m
 
-    def nelectron(self, charge: int = 0) -> int:
+    def nelectron(self, charge: Optional[int] = None) -> int:
+        if charge is None:
+            charge = self.net_charge
         return int(round(float(self.charges.sum()))) - charge
 
 
@@ -215,12 +218,15 @@ def config_high_l(seed: int = 0, nD: int = 1, natm: int = 12, nocc: int = 40) ->
 
 HEAVY_SHELLS = [0, 0, 0, 1, 1, 2]   # 3s2p1d, nuclear charge 6
 LIGHT_SHELLS = [0, 0, 1]            # 2s1p,   nuclear charge 1
+# contraction depths of the 6-31G(d)-like pattern: core s 6, valence s 3 + 1, p 3 + 1, d 1
+HEAVY_DEPTHS = [6, 3, 1, 3, 1, 1]
+LIGHT_DEPTHS = [3, 1, 1]
 
 
-def config_scf(seed: int = 0, natm: int = 120, heavy_fraction: float = 0.3,
-               depth_choices: Tuple[int, int] = (1, 6)) -> Molecule:
-    """120-atom jittered 1.8 A lattice; a seeded 30% of atoms are heavy (3s2p1d, Z=6),
-    the rest light (2s1p, Z=1); depths U{1..6}, a ~ U[0.1, 0.3], beta = 2.5.
+def config_scf(seed: int = 0, natm: int = 120, heavy_fraction: float = 0.3, depths: str = "631gd") -> Molecule:
+    """Jittered 1.8 A lattice; a seeded 30% of atoms are heavy (3s2p1d, Z=6), the rest
+    light (2s1p, Z=1); a ~ U[0.1, 0.3], beta = 2.5.  depths = "631gd" uses the fixed
+    6-31G(d)-like contraction pattern above; depths = "random" draws U{1..6} per shell.
     The returned density is a random PSD placeholder; the SCF driver makes its own."""
     rng = np.random.default_rng(seed)
     coords = lattice_sites(natm, 1.8, 0.2, rng)
@@ -229,10 +235,16 @@ def config_scf(seed: int = 0, natm: int = 120, heavy_fraction: float = 0.3,
     for a in range(natm):
         spec = HEAVY_SHELLS if heavy[a] else LIGHT_SHELLS
         charges[a] = 6.0 if heavy[a] else 1.0
-        shells += _even_tempered_shells(a, spec, 2.5, rng, a_range=(0.1, 0.3),
-                                        depth_choices=depth_choices)
+        if depths == "631gd":
+            dep = HEAVY_DEPTHS if heavy[a] else LIGHT_DEPTHS
+            for l, K in zip(spec, dep):
+                shells += _even_tempered_shells(a, [l], 2.5, rng, a_range=(0.1, 0.3), depth_fixed=K)
+        else:
+            shells += _even_tempered_shells(a, spec, 2.5, rng, a_range=(0.1, 0.3), depth_choices=(1, 6))
     m = _pack("scf", coords, charges, shells, tau=1e-12, seed=seed)
-    nel = m.nelectron()
+    if int(round(charges.sum())) % 2:
+        m.net_charge = 1
+    nel = m.nelectron(m.net_charge)
     nocc = (nel + (nel % 2)) // 2
     m.D = random_psd_density(m.nbf, min(nocc, m.nbf), rng, 1)
     return m
