@@ -78,58 +78,76 @@ class RHF:
         Cocc = C[:, : self.nocc]
         return 2.0 * Cocc @ Cocc.T, e
 
+    # ---- step-wise interface (used by the serving loop): start(), then update(J, K) per build
+    def start(self, diis_space: int = 8, D0=None):
+        """Core-Hamiltonian guess (or D0); returns the first density [nbf, nbf] on the device."""
+        self.diis_space = diis_space
+        self.fs, self.es, self.energies = [], [], []
+        self.e_old = None
+        self.converged = False
+        if D0 is None:
+            self.D, self.mo_e = self._density(self.H)
+        else:
+            self.D, self.mo_e = D0, None
+        return self.D
+
+    def update(self, J, K, conv_tol: Optional[float] = 1e-8):
+        """One SCF step from J, K of the current density: Fock matrix, energy, DIIS, new density.
+        Returns (energy, converged)."""
+        torch = self.torch
+        D = self.D
+        F = self.H + J - 0.5 * K
+        energy = float(0.5 * torch.sum(D * (self.H + F))) + self.enuc
+        self.energies.append(energy)
+        err = self.X.T @ (F @ D @ self.S - self.S @ D @ F) @ self.X
+        self.fs.append(F)
+        self.es.append(err)
+        if len(self.fs) > self.diis_space:
+            self.fs.pop(0)
+            self.es.pop(0)
+        if len(self.fs) >= 2 and float(err.abs().max()) > 1e-13:
+            n = len(self.fs)
+            B = torch.empty((n + 1, n + 1), dtype=torch.float64, device=F.device)
+            for i in range(n):
+                for j in range(i + 1):
+                    B[i, j] = B[j, i] = torch.sum(self.es[i] * self.es[j])
+            B[n, :] = -1.0
+            B[:, n] = -1.0
+            B[n, n] = 0.0
+            rhs = torch.zeros(n + 1, dtype=torch.float64, device=F.device)
+            rhs[n] = -1.0
+            c = torch.linalg.solve(B, rhs)
+            F = sum(c[i] * self.fs[i] for i in range(n))
+        self.D, self.mo_e = self._density(F)
+        if conv_tol is not None and self.e_old is not None and abs(energy - self.e_old) < conv_tol:
+            self.converged = True
+        self.e_old = energy
+        return energy, self.converged
+
     def kernel(self, max_iter: int = 50, conv_tol: float = 1e-8, fixed_iters: Optional[int] = None,
                diis_space: int = 8, D0=None) -> SCFResult:
         torch = self.torch
         t0 = time.perf_counter()
-        if D0 is None:
-            D, mo_e = self._density(self.H)
-        else:
-            D, mo_e = D0, None
+        self.start(diis_space, D0)
         nbf = self.H.shape[0]
         J = torch.empty((1, nbf, nbf), dtype=torch.float64, device=self.H.device)
         K = torch.empty_like(J)
-        fs, es, energies, jk_t = [], [], [], []
-        e_old = None
-        converged = False
+        jk_t = []
         n_iter = fixed_iters if fixed_iters is not None else max_iter
         it = 0
         for it in range(1, n_iter + 1):
             ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             ev0.record()
-            self.plan.jk(D.unsqueeze(0).contiguous(), J, K, stream=self.stream)
+            self.plan.jk(self.D.unsqueeze(0).contiguous(), J, K, stream=self.stream)
             ev1.record()
-            F = self.H + J[0] - 0.5 * K[0]
-            energy = float(0.5 * torch.sum(D * (self.H + F))) + self.enuc
-            energies.append(energy)
+            _, conv = self.update(J[0], K[0], conv_tol if fixed_iters is None else None)
             jk_t.append(ev0.elapsed_time(ev1) / 1e3)
-            err = self.X.T @ (F @ D @ self.S - self.S @ D @ F) @ self.X
-            fs.append(F)
-            es.append(err)
-            if len(fs) > diis_space:
-                fs.pop(0)
-                es.pop(0)
-            if len(fs) >= 2 and float(err.abs().max()) > 1e-13:
-                n = len(fs)
-                B = torch.empty((n + 1, n + 1), dtype=torch.float64, device=F.device)
-                for i in range(n):
-                    for j in range(i + 1):
-                        B[i, j] = B[j, i] = torch.sum(es[i] * es[j])
-                B[n, :] = -1.0
-                B[:, n] = -1.0
-                B[n, n] = 0.0
-                rhs = torch.zeros(n + 1, dtype=torch.float64, device=F.device)
-                rhs[n] = -1.0
-                c = torch.linalg.solve(B, rhs)
-                F = sum(c[i] * fs[i] for i in range(n))
-            D, mo_e = self._density(F)
-            if fixed_iters is None and e_old is not None and abs(energy - e_old) < conv_tol:
-                converged = True
+            if conv:
                 break
-            e_old = energy
         torch.cuda.synchronize()
-        return SCFResult(energy=energies[-1], energies=energies, converged=converged, iterations=it,
-                         jk_seconds=jk_t, total_seconds=time.perf_counter() - t0, D=D, mo_energy=mo_e)
+        return SCFResult(energy=self.energies[-1], energies=list(self.energies), converged=self.converged,
+                         iterations=it, jk_seconds=jk_t, total_seconds=time.perf_counter() - t0, D=self.D,
+                         mo_energy=self.mo_e)
 
 
 def main():
