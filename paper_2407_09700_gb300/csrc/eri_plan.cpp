@@ -649,14 +649,37 @@ eri_status eri_plan_create(const eri_basis* basis, const eri_opts* opts, void* c
     p->nbf += sh_n[i];
   }
 
-  // ---- shell pairs (i >= j) in canonical orientation, grouped by type and depth
-  struct Tmp { int t, np, i, j; };
+  // ---- shell pairs (i >= j) in canonical orientation, grouped by type and depth.
+  // A primitive pair whose Gaussian-product factor exp(-ab/(a+b) |A-B|^2) is below 1e-30
+  // (exponent argument above PRIM_PAIR_CUT) is dropped: with contraction coefficients and
+  // polynomial factors each below ~1e4 its contribution to any integral stays under 1e-22,
+  // far below FP64 resolution of the retained terms.  Each shell pair keeps at least its
+  // primitive pair of largest factor.
+  const double PRIM_PAIR_CUT = 69.0;
+  struct Tmp { int t, np, i, j; std::vector<int> keep; };
   std::vector<Tmp> tmp;
   for (int i = 0; i < p->nshell; ++i)
     for (int j = 0; j <= i; ++j) {
       int a = i, b = j;
       if (p->sh_l[b] > p->sh_l[a]) std::swap(a, b);
-      tmp.push_back({ptype_of(p->sh_l[a], p->sh_l[b]), p->sh_nprim[a] * p->sh_nprim[b], a, b});
+      const double* A = &p->coords[3 * p->sh_atom[a]];
+      const double* B = &p->coords[3 * p->sh_atom[b]];
+      double AB2 = 0.0;
+      for (int x = 0; x < 3; ++x) AB2 += (A[x] - B[x]) * (A[x] - B[x]);
+      Tmp t{ptype_of(p->sh_l[a], p->sh_l[b]), 0, a, b, {}};
+      int best = 0;
+      double best_arg = 1e300;
+      for (int u = 0; u < p->sh_nprim[a]; ++u)
+        for (int v = 0; v < p->sh_nprim[b]; ++v) {
+          const double al = p->exps[p->sh_off[a] + u], be = p->exps[p->sh_off[b] + v];
+          const double arg = al * be / (al + be) * AB2;
+          const int code = u * p->sh_nprim[b] + v;
+          if (arg <= PRIM_PAIR_CUT) t.keep.push_back(code);
+          if (arg < best_arg) { best_arg = arg; best = code; }
+        }
+      if (t.keep.empty()) t.keep.push_back(best);
+      t.np = (int)t.keep.size();
+      tmp.push_back(std::move(t));
     }
   std::stable_sort(tmp.begin(), tmp.end(), [](const Tmp& x, const Tmp& y) {
     return x.t != y.t ? x.t < y.t : x.np > y.np;
@@ -682,21 +705,21 @@ eri_status eri_plan_create(const eri_basis* basis, const eri_opts* opts, void* c
       sp.AB[x] = A[x] - B[x];
       AB2 += sp.AB[x] * sp.AB[x];
     }
-    for (int u = 0; u < p->sh_nprim[t.i]; ++u)
-      for (int v = 0; v < p->sh_nprim[t.j]; ++v) {
-        const double al = p->exps[p->sh_off[t.i] + u], be = p->exps[p->sh_off[t.j] + v];
-        const double ca = p->coefs[p->sh_off[t.i] + u], cb = p->coefs[p->sh_off[t.j] + v];
-        PrimPair pp;
-        pp.zeta = al + be;
-        for (int x = 0; x < 3; ++x) {
-          pp.P[x] = (al * A[x] + be * B[x]) / pp.zeta;
-          pp.PA[x] = pp.P[x] - A[x];
-        }
-        pp.E = pref / pp.zeta * std::exp(-al * be / pp.zeta * AB2) * ca * cb;
-        pp.hz = 0.5 / pp.zeta;
-        pp.pad = 0.0;
-        p->prims.push_back(pp);
+    for (int code : t.keep) {
+      const int u = code / p->sh_nprim[t.j], v = code % p->sh_nprim[t.j];
+      const double al = p->exps[p->sh_off[t.i] + u], be = p->exps[p->sh_off[t.j] + v];
+      const double ca = p->coefs[p->sh_off[t.i] + u], cb = p->coefs[p->sh_off[t.j] + v];
+      PrimPair pp;
+      pp.zeta = al + be;
+      for (int x = 0; x < 3; ++x) {
+        pp.P[x] = (al * A[x] + be * B[x]) / pp.zeta;
+        pp.PA[x] = pp.P[x] - A[x];
       }
+      pp.E = pref / pp.zeta * std::exp(-al * be / pp.zeta * AB2) * ca * cb;
+      pp.hz = 0.5 / pp.zeta;
+      pp.pad = 0.0;
+      p->prims.push_back(pp);
+    }
     p->pairs_all.push_back(sp);
     p->pair_index[(size_t)t.i * p->nshell + t.j] = (int)k;
     p->pair_index[(size_t)t.j * p->nshell + t.i] = (int)k;
