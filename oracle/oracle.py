@@ -103,14 +103,15 @@ def normalise(mol) -> np.ndarray:
 class OracleBasis:
     """Keeps the contiguous arrays alive while the C side holds pointers to them."""
 
-    def __init__(self, mol):
+    def __init__(self, mol, coefs=None):
+        """coefs: final contraction coefficients (skips the normalisation) or None."""
         self.coords = np.ascontiguousarray(mol.coords, dtype=np.float64)
         self.atom = np.ascontiguousarray(mol.shell_atom, dtype=np.int32)
         self.l = np.ascontiguousarray(mol.shell_l, dtype=np.int32)
         self.nprim = np.ascontiguousarray(mol.shell_nprim, dtype=np.int32)
         self.off = np.ascontiguousarray(mol.shell_off, dtype=np.int32)
         self.exps = np.ascontiguousarray(mol.exps, dtype=np.float64)
-        self.coefs = np.ascontiguousarray(normalise(mol), dtype=np.float64)
+        self.coefs = np.ascontiguousarray(normalise(mol) if coefs is None else coefs, dtype=np.float64)
         self.nshell = int(self.l.shape[0])
         self.nbf = int(sum((int(x) + 1) * (int(x) + 2) // 2 for x in self.l))
         self.D = getattr(mol, "D", None)
