@@ -145,6 +145,28 @@ eri_status eri_jk_host(eri_plan* plan, const double* D, int nD, double* J, doubl
                        void* cuda_stream);
 
 /*
+ * Nuclear gradients of the Coulomb and exchange energies for one fixed density
+ * (Sec. 4, Eqs. 10-14, Alg. 4):
+ *   E_J = 1/2 sum_abcd (ab|cd) D_ab D_cd,   E_K = -1/4 sum_abcd (ab|cd) D_ac D_bd,
+ * so that for a closed-shell density E_J + E_K is the two-electron energy
+ * 1/2 tr(D J) - 1/4 tr(D K).  gJ[A][x] = dE_J/dR_Ax and gK[A][x] = dE_K/dR_Ax with D
+ * held fixed (the ERI-derivative part of the RHF gradient).  The ERI derivatives are
+ * contracted with the density products inside the kernels; no derivative Fock matrix
+ * is formed.  Unique shell quartets with the plan's screening as in eri_jk (a quartet is
+ * evaluated when Q_ij * Q_kl * max|D| over its six cross blocks >= tau).  FP64 for every
+ * plan precision.
+ * D: DEVICE pointer, [nbf][nbf] FP64, symmetric (not checked).  gJ, gK: DEVICE
+ * pointers, [natm][3] FP64 each, overwritten.  Asynchronous on cuda_stream; shares the
+ * plan's scratch with eri_jk (calls on one plan must not overlap on the GPU).
+ * Errors: ERI_ERR_ARG (NULL pointers), ERI_ERR_OOM, ERI_ERR_CUDA.
+ */
+eri_status eri_jk_grad(eri_plan* plan, const double* D, double* gJ, double* gK, void* cuda_stream);
+
+/* Shell quartets and primitive quartets evaluated by the last eri_jk_grad call
+ * (synchronises that call's stream). */
+eri_status eri_grad_stats(eri_plan* plan, long long* quartets, long long* prim_quartets);
+
+/*
  * One contracted shell quartet (ij|kl) by Rys quadrature (Eq. 1 contracted by
  * Eq. 5), no screening: writes n_i*n_j*n_k*n_l FP64 values in (i,j,k,l)
  * row-major Cartesian order to out (HOST memory).  Synchronous.

@@ -34,7 +34,7 @@
 #include <omp.h>
 #endif
 
-#define ORC_LMAX 4
+#define ORC_LMAX 5   /* l <= 4 shells and their l+1 derivative companions */
 #define ORC_MMAX (4 * ORC_LMAX + 1)
 
 /* ------------------------------------------------------------------ Cartesian indexing */

@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liberi.so")
-SOURCES = ["eri_kernels.cu", "eri_small.cu", "eri_plan.cpp", "rys_table.cpp", "eri_noalloc.cu", "eri_onee.cpp"]
+SOURCES = ["eri_kernels.cu", "eri_small.cu", "eri_grad.cu", "eri_plan.cpp", "rys_table.cpp", "eri_noalloc.cu", "eri_onee.cpp"]
 HEADERS = ["eri_internal.h", "rys_table.h", "eri_device.cuh", os.path.join("..", "..", "include", "eri.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

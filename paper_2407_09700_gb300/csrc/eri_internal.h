@@ -5,7 +5,8 @@
 
 #define ERI_LMAX 4
 #define ERI_NPAIRTYPE 15          // canonical pair types (l0 >= l1), l <= 4
-#define ERI_MAXCART 165           // Cartesian triples with l <= 8
+#define ERI_CART_LMAX 9           // Cartesian tables cover l <= 9 (gradient transfer of (gg| reaches 9)
+#define ERI_MAXCART 220           // Cartesian triples with l <= 9
 
 // One primitive pair (Gaussian product of Eq. 2's primitives on the pair's two
 // centres A, B).  80 bytes, 16-byte aligned.
@@ -15,7 +16,7 @@ struct PrimPair {
   double PA[3];    // P - A
   double E;        // sqrt(2) pi^(5/4) / zeta * exp(-alpha beta |A-B|^2 / zeta) * c_alpha c_beta
   double hz;       // 1 / (2 zeta)
-  double pad;
+  double alpha;    // exponent of the primitive on A (the gradient kernels weight by 2 alpha, 2 beta)
 };
 
 // FP32 shadow of PrimPair for the FP32 path of the mixed mode.  40 bytes.
@@ -123,6 +124,37 @@ struct KernelArgs {
   double rys_tcut_d;           // the same cutoff as a double
 };
 
+// One angular-momentum class of the two-electron energy gradient (Sec. 4, Eqs. 11-14).
+// The 2D tables run to Le2 = la+lb+1, Lf2 = lc+ld+1 with nroots = floor((L+1)/2) + 1.
+// Four contracted sets of [e0|f0] are assembled, concatenated in this order, each stored
+// [e][f] row-major with e, f relative to the set's first Cartesian:
+//   set 0  weight 1      e in [max(la-1,0), Le],  f in [max(lc-1,0), Lf]
+//   set 1  weight 2 alpha e in [la+1, Le+1],      f in [lc, Lf]
+//   set 2  weight 2 beta  e in [la, Le+1],        f in [lc, Lf]
+//   set 3  weight 2 gamma e in [la, Le],          f in [lc+1, Lf+1]
+// (alpha, beta, gamma: exponents of the primitives on centres A, B, C).
+struct GradDesc {
+  int la, lb, lc, ld;
+  int na, nb, nc, nd;
+  int nroots, Le2, Lf2, nI;
+  int s_elo[4], s_ne[4], s_flo[4], s_nf[4];   // first l and Cartesian count of e / f per set
+  int s_off[4];                               // offset of each set in the team scratch
+  int nout;                                   // total assembled values (sum of the four sets)
+  int npass, bp, team_doubles;
+  int gam_off;                                // Gamma_J, Gamma_K: 2 * na nb nc nd doubles
+  int hrr_off, hrr_doubles;                   // two HRR ping-pong buffers
+  long long scratch_per_team;
+  const uint32_t* outidx;                     // [nout] ix | iy << 8 | iz << 16 | set << 24
+};
+
+struct GradArgs {
+  KernelArgs k;          // task space, pair data, compacted list, Rys table of nroots
+  GradDesc g;
+  const int* sh_atom;    // [nshell] atom of each shell
+  double* gJ;            // [natm][3] += d E_J / d R
+  double* gK;            // [natm][3] += d E_K / d R
+};
+
 // Host-side launchers implemented in eri_kernels.cu.  All return a cudaError_t as int.
 #ifdef __cplusplus
 extern "C" {
@@ -147,6 +179,10 @@ int erik_upload_cart_tables_small(void);
 int erik_small_available(int la, int lb, int lc, int ld);
 int erik_small_blocks_per_sm(int la, int lb, int lc, int ld, int fp32, int* out);
 int erik_launch_small(int la, int lb, int lc, int ld, int fp32, const struct KernelArgs* a, int grid, void* stream);
+// energy-gradient class kernels (eri_grad.cu)
+int erik_upload_cart_tables_grad(void);
+int erik_grad_blocks_per_sm(int ts, int smem_bytes, int* out);
+int erik_launch_grad(int ts, const struct GradArgs* a, int grid, int smem_bytes, void* stream);
 #ifdef __cplusplus
 }
 #endif

@@ -454,7 +454,7 @@ __global__ void fma_probe_kernel(Tp* out, int iters, Tp a, Tp b) {
 extern "C" int erik_upload_cart_tables(void) {
   unsigned char h[ERI_MAXCART][4];
   int g = 0;
-  for (int l = 0; l <= 8; ++l)
+  for (int l = 0; l <= ERI_CART_LMAX; ++l)
     for (int lx = l; lx >= 0; --lx)
       for (int ly = l - lx; ly >= 0; --ly) {
         h[g][0] = (unsigned char)lx;

@@ -58,12 +58,12 @@ inline void ptype_ls(int t, int* l0, int* l1) {
   *l1 = t - a * (a + 1) / 2;
 }
 
-// Cartesian triples in x-descending order, l = 0..8 (host copy of the device table).
+// Cartesian triples in x-descending order, l = 0..9 (host copy of the device table).
 struct CartTab {
   int lx[ERI_MAXCART], ly[ERI_MAXCART], lz[ERI_MAXCART];
   CartTab() {
     int g = 0;
-    for (int l = 0; l <= 8; ++l)
+    for (int l = 0; l <= ERI_CART_LMAX; ++l)
       for (int x = l; x >= 0; --x)
         for (int y = l - x; y >= 0; --y) {
           lx[g] = x;
@@ -87,6 +87,9 @@ struct DeviceState {
   uint32_t* outidx = nullptr;        // all 225 class index tables
   ClassDesc classes[ERI_NPAIRTYPE][ERI_NPAIRTYPE];
   int ts[ERI_NPAIRTYPE][ERI_NPAIRTYPE];
+  uint32_t* grad_outidx = nullptr;   // all gradient class index tables
+  GradDesc gclasses[ERI_NPAIRTYPE][ERI_NPAIRTYPE];
+  int gts[ERI_NPAIRTYPE][ERI_NPAIRTYPE];
   int sms = 0;
 };
 std::mutex g_dev_mu;
@@ -149,6 +152,73 @@ void make_class(int la, int lb, int lc, int ld, ClassDesc* c, int* ts, std::vect
   c->outidx = nullptr;
 }
 
+// Fill the static part of a gradient class descriptor (Sec. 4): the four contracted sets,
+// their 2D-table offsets tagged with the set, team sizes and the scratch layout.
+void make_grad_class(int la, int lb, int lc, int ld, GradDesc* g, int* ts, std::vector<uint32_t>* idx) {
+  memset(g, 0, sizeof(*g));
+  g->la = la; g->lb = lb; g->lc = lc; g->ld = ld;
+  g->na = ncart(la); g->nb = ncart(lb); g->nc = ncart(lc); g->nd = ncart(ld);
+  const int Le = la + lb, Lf = lc + ld;
+  g->nroots = (Le + Lf + 1) / 2 + 1;
+  g->Le2 = Le + 1;
+  g->Lf2 = Lf + 1;
+  g->nI = (g->Le2 + 1) * (g->Lf2 + 1);
+  const int elo[4] = {std::max(la - 1, 0), la + 1, la, la}, ehi[4] = {Le, Le + 1, Le + 1, Le};
+  const int flo[4] = {std::max(lc - 1, 0), lc, lc, lc + 1}, fhi[4] = {Lf, Lf, Lf, Lf + 1};
+  const CartTab& ct = cart();
+  const int L1 = g->Lf2 + 1;
+  idx->clear();
+  int off = 0;
+  for (int k = 0; k < 4; ++k) {
+    g->s_elo[k] = elo[k];
+    g->s_flo[k] = flo[k];
+    g->s_ne[k] = cart_below(ehi[k] + 1) - cart_below(elo[k]);
+    g->s_nf[k] = cart_below(fhi[k] + 1) - cart_below(flo[k]);
+    g->s_off[k] = off;
+    for (int ie = 0; ie < g->s_ne[k]; ++ie)
+      for (int jf = 0; jf < g->s_nf[k]; ++jf) {
+        const int e = cart_below(elo[k]) + ie, f = cart_below(flo[k]) + jf;
+        const uint32_t ix = ct.lx[e] * L1 + ct.lx[f];
+        const uint32_t iy = ct.ly[e] * L1 + ct.ly[f];
+        const uint32_t iz = ct.lz[e] * L1 + ct.lz[f];
+        idx->push_back(ix | (iy << 8) | (iz << 16) | ((uint32_t)k << 24));
+      }
+    off += g->s_ne[k] * g->s_nf[k];
+  }
+  g->nout = off;
+  *ts = choose_ts(g->nout);
+  g->npass = (g->nout + *ts * 32 - 1) / (*ts * 32);
+  const int per_prim = 4 + 21 + 3 * g->nroots * g->nI;
+  if (*ts == 1) {
+    g->bp = 1;
+  } else {
+    const int budget = (*ts == 8) ? 768 : 3072;
+    g->bp = std::max(1, std::min(32, budget / per_prim));
+  }
+  g->team_doubles = g->bp * per_prim;
+  const int nabcd = g->na * g->nb * g->nc * g->nd;
+  g->gam_off = (off + 1) & ~1;
+  g->hrr_off = g->gam_off + ((2 * nabcd + 1) & ~1);
+  // largest level of the six transfer sequences: bra (la', lb') over the ket shell's
+  // columns, then ket (lc', ld') over the bra block
+  long long m = 1;
+  auto seq = [&](int a_, int b_, int c_, int d_) {
+    const long long nv = cart_below(c_ + d_ + 1) - cart_below(c_);
+    for (int k = 1; k <= b_; ++k) m = std::max(m, (long long)(cart_below(a_ + b_ - k + 1) - cart_below(a_)) * ncart(k) * nv);
+    const long long nab = (long long)ncart(a_) * ncart(b_);
+    for (int k = 1; k <= d_; ++k) m = std::max(m, (long long)(cart_below(c_ + d_ - k + 1) - cart_below(c_)) * ncart(k) * nab);
+  };
+  seq(la + 1, lb, lc, ld);
+  if (la > 0) seq(la - 1, lb, lc, ld);
+  seq(la, lb + 1, lc, ld);
+  if (lb > 0) seq(la, lb - 1, lc, ld);
+  seq(la, lb, lc + 1, ld);
+  if (lc > 0) seq(la, lb, lc - 1, ld);
+  g->hrr_doubles = (int)((m + 1) & ~1LL);
+  g->scratch_per_team = (long long)g->hrr_off + 2LL * g->hrr_doubles;
+  g->outidx = nullptr;
+}
+
 eri_status device_init(int dev, DeviceState** out) {
   std::lock_guard<std::mutex> lk(g_dev_mu);
   if (dev < 0 || dev >= 64) return fail(ERI_ERR_ARG, "device index %d out of range", dev);
@@ -156,6 +226,7 @@ eri_status device_init(int dev, DeviceState** out) {
   if (!s.ready) {
     CUDA_TRY(erik_upload_cart_tables());
     CUDA_TRY(erik_upload_cart_tables_small());
+    CUDA_TRY(erik_upload_cart_tables_grad());
     size_t ncoef = (size_t)RYS_NCOEF, nas = (size_t)RYS_ASYM_OFFSET[RYS_NMAX] + RYS_NMAX;
     CUDA_TRY(cudaMalloc(&s.rys_coef, sizeof(double) * ncoef));
     CUDA_TRY(cudaMalloc(&s.rys_au, sizeof(double) * nas));
@@ -178,6 +249,20 @@ eri_status device_init(int dev, DeviceState** out) {
     CUDA_TRY(cudaMemcpy(s.outidx, all.data(), sizeof(uint32_t) * all.size(), cudaMemcpyHostToDevice));
     for (int X = 0; X < ERI_NPAIRTYPE; ++X)
       for (int Y = 0; Y < ERI_NPAIRTYPE; ++Y) s.classes[X][Y].outidx = s.outidx + offs[X][Y];
+    all.clear();
+    for (int X = 0; X < ERI_NPAIRTYPE; ++X)
+      for (int Y = 0; Y < ERI_NPAIRTYPE; ++Y) {
+        int la, lb, lc, ld;
+        ptype_ls(X, &la, &lb);
+        ptype_ls(Y, &lc, &ld);
+        make_grad_class(la, lb, lc, ld, &s.gclasses[X][Y], &s.gts[X][Y], &one);
+        offs[X][Y] = all.size();
+        all.insert(all.end(), one.begin(), one.end());
+      }
+    CUDA_TRY(cudaMalloc(&s.grad_outidx, sizeof(uint32_t) * all.size()));
+    CUDA_TRY(cudaMemcpy(s.grad_outidx, all.data(), sizeof(uint32_t) * all.size(), cudaMemcpyHostToDevice));
+    for (int X = 0; X < ERI_NPAIRTYPE; ++X)
+      for (int Y = 0; Y < ERI_NPAIRTYPE; ++Y) s.gclasses[X][Y].outidx = s.grad_outidx + offs[X][Y];
     CUDA_TRY(cudaDeviceGetAttribute(&s.sms, cudaDevAttrMultiProcessorCount, dev));
     s.ready = true;
   }
@@ -285,6 +370,7 @@ struct eri_plan {
   PrimPairF* d_primsf = nullptr;
   int* d_sh_bf0 = nullptr;
   int* d_sh_n = nullptr;
+  int* d_sh_atom = nullptr;
   double* d_Dmax = nullptr;
   unsigned long long* d_counters = nullptr;   // one per class launch
   unsigned long long* d_stats = nullptr;      // [2][256][2]: FP64 launches, then FP32 launches
@@ -301,6 +387,8 @@ struct eri_plan {
   size_t tlist_cap = 0;
   unsigned long long* d_tcount = nullptr;     // [256][2] FP64 / FP32 list lengths
   unsigned* d_tiles = nullptr;                // per-tile counts / offsets of the compaction
+  unsigned long long* d_gstats = nullptr;     // [2] quartets / primitive quartets of eri_jk_grad
+  cudaStream_t grad_stream = nullptr;
   size_t tiles_cap = 0;
   size_t host_io_cap = 0;
   cudaStream_t last_stream = nullptr;
@@ -598,9 +686,9 @@ eri_status eri_plan_destroy(eri_plan* p) {
   cudaSetDevice(p->device);
   cudaDeviceSynchronize();
   for (cudaEvent_t e : p->events) cudaEventDestroy(e);
-  void* bufs[] = {p->d_pairs_all, p->d_pairs, p->d_prims, p->d_primsf, p->d_sh_bf0, p->d_sh_n, p->d_Dmax, p->d_counters,
+  void* bufs[] = {p->d_pairs_all, p->d_pairs, p->d_prims, p->d_primsf, p->d_sh_bf0, p->d_sh_n, p->d_sh_atom, p->d_Dmax, p->d_counters,
                   p->d_stats, p->d_scratch, p->d_tasks, p->d_out, p->d_off, p->d_host_io, p->d_tlist,
-                  p->d_tcount, p->d_tiles};
+                  p->d_tcount, p->d_tiles, p->d_gstats};
   for (void* b : bufs)
     if (b) cudaFree(b);
   delete p;
@@ -717,7 +805,7 @@ eri_status eri_plan_create(const eri_basis* basis, const eri_opts* opts, void* c
       }
       pp.E = pref / pp.zeta * std::exp(-al * be / pp.zeta * AB2) * ca * cb;
       pp.hz = 0.5 / pp.zeta;
-      pp.pad = 0.0;
+      pp.alpha = al;
       p->prims.push_back(pp);
     }
     p->pairs_all.push_back(sp);
@@ -735,6 +823,7 @@ eri_status eri_plan_create(const eri_basis* basis, const eri_opts* opts, void* c
       cudaMalloc(&p->d_primsf, sizeof(PrimPairF) * p->prims.size()) != cudaSuccess ||
       cudaMalloc(&p->d_sh_bf0, sizeof(int) * p->nshell) != cudaSuccess ||
       cudaMalloc(&p->d_sh_n, sizeof(int) * p->nshell) != cudaSuccess ||
+      cudaMalloc(&p->d_sh_atom, sizeof(int) * p->nshell) != cudaSuccess ||
       cudaMalloc(&p->d_Dmax, sizeof(double) * p->nshell * p->nshell) != cudaSuccess ||
       cudaMalloc(&p->d_counters, sizeof(unsigned long long) * 256) != cudaSuccess ||
       cudaMalloc(&p->d_stats, sizeof(unsigned long long) * 4 * 256) != cudaSuccess ||
@@ -766,6 +855,7 @@ eri_status eri_plan_create(const eri_basis* basis, const eri_opts* opts, void* c
   PLAN_TRY(cudaMemcpy(p->d_primsf, primsf.data(), sizeof(PrimPairF) * primsf.size(), cudaMemcpyHostToDevice));
   PLAN_TRY(cudaMemcpyAsync(p->d_sh_bf0, p->sh_bf0.data(), sizeof(int) * p->nshell, cudaMemcpyHostToDevice, st));
   PLAN_TRY(cudaMemcpyAsync(p->d_sh_n, sh_n.data(), sizeof(int) * p->nshell, cudaMemcpyHostToDevice, st));
+  PLAN_TRY(cudaMemcpyAsync(p->d_sh_atom, p->sh_atom.data(), sizeof(int) * p->nshell, cudaMemcpyHostToDevice, st));
   PLAN_TRY(cudaMemsetAsync(p->d_stats, 0, sizeof(unsigned long long) * 4 * 256, st));
 
   // ---- Schwarz factors (Eq. 7) from the diagonal quartets (ij|ij), one class (X|X) at a time
@@ -823,6 +913,107 @@ eri_status eri_jk(eri_plan* p, const double* D, int nD, double* J, double* K, in
   if ((s = ensure_buf(&p->d_tlist, &p->tlist_cap, maxnt)) != ERI_OK) return s;
   if ((s = ensure_buf(&p->d_tiles, &p->tiles_cap, 2 * ((maxnt + 1023) / 1024 + 1))) != ERI_OK) return s;
   return run_jk(p, launches, D, nD, J, K, flags & 3, (cudaStream_t)cuda_stream, p->d_scratch, true, true);
+}
+
+eri_status eri_jk_grad(eri_plan* p, const double* D, double* gJ, double* gK, void* cuda_stream) {
+  g_err.clear();
+  if (!p) return fail(ERI_ERR_ARG, "plan is NULL");
+  if (!D || !gJ || !gK) return fail(ERI_ERR_ARG, "D, gJ and gK must be non-NULL");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  struct GL { int X, Y, ts, grid, smem; long long nt; };
+  std::vector<GL> ls;
+  size_t need = 0, maxnt = 1;
+  for (int X = 0; X < ERI_NPAIRTYPE; ++X) {
+    if (!p->type_cnt[X]) continue;
+    for (int Y = 0; Y <= X; ++Y) {
+      if (!p->type_cnt[Y]) continue;
+      const long long nx = p->type_cnt[X], ny = p->type_cnt[Y];
+      const long long nt = (X == Y) ? nx * (nx + 1) / 2 : nx * ny;
+      if ((unsigned long long)nt > 0xffffffffULL) return fail(ERI_ERR_ARG, "class task space above 2^32");
+      const GradDesc& g = p->dev->gclasses[X][Y];
+      GL l{X, Y, p->dev->gts[X][Y], 0, 0, nt};
+      const int tpb = 128 / l.ts;
+      l.smem = (int)(sizeof(double) * (size_t)g.team_doubles * tpb);
+      if (l.smem > 200 * 1024)
+        return fail(ERI_ERR_ARG, "gradient class (%d%d|%d%d) needs %d bytes of shared memory", g.la, g.lb, g.lc, g.ld, l.smem);
+      int bps = 0;
+      CUDA_TRY(erik_grad_blocks_per_sm(l.ts, l.smem, &bps));
+      if (bps < 1) bps = 1;
+      l.grid = (int)std::max(1LL, std::min((long long)p->dev->sms * bps, (nt + tpb - 1) / tpb));
+      need = std::max(need, (size_t)l.grid * tpb * (size_t)g.scratch_per_team);
+      maxnt = std::max(maxnt, (size_t)nt);
+      ls.push_back(l);
+    }
+  }
+  eri_status s;
+  if ((s = ensure_scratch(p, need)) != ERI_OK) return s;
+  if ((s = ensure_buf(&p->d_tlist, &p->tlist_cap, maxnt)) != ERI_OK) return s;
+  if ((s = ensure_buf(&p->d_tiles, &p->tiles_cap, 2 * ((maxnt + 1023) / 1024 + 1))) != ERI_OK) return s;
+  if (!p->d_gstats) CUDA_TRY(cudaMalloc(&p->d_gstats, sizeof(unsigned long long) * 2));
+  CUDA_TRY(cudaMemsetAsync(gJ, 0, sizeof(double) * 3 * p->natm, st));
+  CUDA_TRY(cudaMemsetAsync(gK, 0, sizeof(double) * 3 * p->natm, st));
+  CUDA_TRY(cudaMemsetAsync(p->d_gstats, 0, sizeof(unsigned long long) * 2, st));
+  CUDA_TRY(erik_launch_dmax(D, 1, p->nbf, p->nshell, p->d_sh_bf0, p->d_sh_n, p->d_Dmax, st));
+  CUDA_TRY(cudaMemsetAsync(p->d_counters, 0, sizeof(unsigned long long) * 256, st));
+  CUDA_TRY(cudaMemsetAsync(p->d_tcount, 0, sizeof(unsigned long long) * 2 * 256, st));
+  int li = 0;
+  for (const GL& l : ls) {
+    const GradDesc& g = p->dev->gclasses[l.X][l.Y];
+    KernelArgs a = base_args(p, l.X, l.Y);
+    const int N = g.nroots;
+    a.rys_coef = p->dev->rys_coef + RYS_COEF_OFFSET[N];
+    a.rys_au = p->dev->rys_au + RYS_ASYM_OFFSET[N];
+    a.rys_aw = p->dev->rys_aw + RYS_ASYM_OFFSET[N];
+    a.rys_tcut = RYS_TCUT[N];
+    a.rys_tcut_d = (double)RYS_TCUT[N];
+    a.pairs = p->d_pairs;
+    a.bra0 = p->type_off[l.X];
+    a.nbra = p->type_cnt[l.X];
+    a.ket0 = p->type_off[l.Y];
+    a.nket = p->type_cnt[l.Y];
+    a.tri = (l.X == l.Y);
+    a.ntask = l.nt;
+    a.Dmax = p->d_Dmax;
+    a.tau = p->opts.screen_thresh;
+    a.prec_sel = 0;
+    a.D = D;
+    a.nD = 1;
+    a.want = 3;
+    a.mode = KMODE_JK;
+    a.counter = p->d_counters + li;
+    a.scratch = p->d_scratch;
+    a.stats = p->d_gstats;
+    unsigned long long* cnt = p->d_tcount + 2 * li;
+    CUDA_TRY(erik_launch_compact(&a, p->d_tlist, (unsigned long long)l.nt, cnt, p->d_tiles, 0, st));
+    a.tlist = p->d_tlist;
+    a.list_cap = (unsigned long long)l.nt;
+    a.from_back = 0;
+    a.tcount = cnt;
+    GradArgs ga;
+    memset(&ga, 0, sizeof(ga));
+    ga.k = a;
+    ga.g = g;
+    ga.sh_atom = p->d_sh_atom;
+    ga.gJ = gJ;
+    ga.gK = gK;
+    CUDA_TRY(erik_launch_grad(l.ts, &ga, l.grid, l.smem, st));
+    ++li;
+  }
+  p->grad_stream = st;
+  return ERI_OK;
+}
+
+eri_status eri_grad_stats(eri_plan* p, long long* quartets, long long* prim_quartets) {
+  g_err.clear();
+  if (!p || !quartets || !prim_quartets) return fail(ERI_ERR_ARG, "NULL argument");
+  unsigned long long h[2] = {0, 0};
+  if (p->d_gstats) {
+    CUDA_TRY(cudaStreamSynchronize(p->grad_stream));
+    CUDA_TRY(cudaMemcpy(h, p->d_gstats, sizeof(h), cudaMemcpyDeviceToHost));
+  }
+  *quartets = (long long)h[0];
+  *prim_quartets = (long long)h[1];
+  return ERI_OK;
 }
 
 eri_status eri_jk_host(eri_plan* p, const double* D, int nD, double* J, double* K, int flags, void* cuda_stream) {

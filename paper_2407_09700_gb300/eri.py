@@ -71,6 +71,9 @@ _SIGS = {
     "eri_jk_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                       ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "eri_jk_host": (ctypes.c_int, [ctypes.c_void_p, _dp, ctypes.c_int, _dp, _dp, ctypes.c_int, ctypes.c_void_p]),
+    "eri_jk_grad": (ctypes.c_int, [ctypes.c_void_p] * 5),
+    "eri_grad_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong),
+                                      ctypes.POINTER(ctypes.c_longlong)]),
     "eri_shell_quartet": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int] * 4 + [_dp]),
     "eri_schwarz": (ctypes.c_int, [ctypes.c_void_p, _dp]),
     "eri_rys_roots": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp]),
@@ -198,6 +201,26 @@ class Plan:
             J = J[0] if J is not None else None
             K = K[0] if K is not None else None
         return J, K
+
+    def jk_grad(self, D, gJ=None, gK=None, stream=None):
+        """Gradients [natm, 3] of E_J = 1/2 sum (ab|cd) D_ab D_cd and E_K = -1/4 sum (ab|cd) D_ac D_bd
+        with D (CUDA float64 [nbf, nbf], symmetric) held fixed; asynchronous."""
+        import torch
+        if D.dtype != torch.float64 or not D.is_cuda or not D.is_contiguous() or D.dim() != 2:
+            raise ValueError("D must be a contiguous CUDA float64 [nbf, nbf] tensor")
+        natm = int(self._arrs["coords"].shape[0])
+        if gJ is None:
+            gJ = torch.empty((natm, 3), dtype=torch.float64, device=D.device)
+        if gK is None:
+            gK = torch.empty((natm, 3), dtype=torch.float64, device=D.device)
+        _check(load_library().eri_jk_grad(self._h, ctypes.c_void_p(D.data_ptr()), ctypes.c_void_p(gJ.data_ptr()),
+                                          ctypes.c_void_p(gK.data_ptr()), _stream_handle(stream)))
+        return gJ, gK
+
+    def grad_stats(self):
+        q, pq = ctypes.c_longlong(), ctypes.c_longlong()
+        _check(load_library().eri_grad_stats(self._h, ctypes.byref(q), ctypes.byref(pq)))
+        return {"quartets": q.value, "prim_quartets": pq.value}
 
     # -- host path (copies inside)
     def jk_host(self, D, want=ERI_WANT_J | ERI_WANT_K, stream=0):

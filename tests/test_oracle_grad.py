@@ -22,7 +22,8 @@ def _mol(seed, ls_per_atom, natm=3):
     return m
 
 
-@pytest.mark.parametrize("seed,ls", [(0, [(0, 1), (1,), (0,)]), (1, [(2,), (0, 1)]), (2, [(1, 2), (3,)])])
+@pytest.mark.parametrize("seed,ls", [(0, [(0, 1), (1,), (0,)]), (1, [(2,), (0, 1)]), (2, [(1, 2), (3,)]),
+                                     (3, [(4,), (0,)])])
 def test_gradient_matches_finite_differences(seed, ls):
     m = _mol(seed, ls, natm=3 if len(ls) > 2 else 2)
     gJ, gK = grad_ref.jk_grad(m, m.D)
