@@ -187,7 +187,7 @@ eri_status eri_rys_roots(int N, int n, const double* T, double* u, double* w);
 /* Per-launch record of the last eri_jk call when profiling is on. */
 typedef struct {
   int la, lb, lc, ld;             /* class of the launch */
-  int team_size;                  /* threads per shell quartet (1, 8 or 32) */
+  int team_size;                  /* threads per shell quartet (1, 2, 4, 8 or 32) */
   int grid;                       /* blocks launched */
   float ms;                       /* CUDA-event time of the launch on the call's stream */
   long long quartets;             /* shell quartets evaluated (after screening) */

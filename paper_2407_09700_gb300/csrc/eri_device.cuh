@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include "eri_internal.h"
+#include "rys_table.h"
 
 #define TPB 128        // threads per block of the class kernels
 #define GSLOTS 32      // accumulator slots per lane
@@ -30,10 +31,11 @@ struct Smem {
 };
 
 // ------------------------------------------------------------------ Rys roots and weights
-__device__ __forceinline__ double horner12(const double* __restrict__ c, double x) {
+// Degree-RYS_DEG polynomial, highest power first, by Horner's rule.
+__device__ __forceinline__ double horner_rys(const double* __restrict__ c, double x) {
   double a = __ldg(c);
 #pragma unroll
-  for (int k = 1; k <= 11; ++k) a = fma(a, x, __ldg(c + k));
+  for (int k = 1; k <= RYS_DEG; ++k) a = fma(a, x, __ldg(c + k));
   return a;
 }
 
@@ -46,11 +48,12 @@ __device__ __forceinline__ int floor_nonneg(double T) {
   return (int)(m >> (52 - e));
 }
 
-// Prepare the table lookup for one T: ti >= 0 selects interval ti, else the large-T limit.
+// Prepare the table lookup for one T: ti >= 0 selects interval ti (of width 1/RYS_SUB),
+// else the large-T limit.
 __device__ __forceinline__ void rys_locate(double T, double tcut, int& ti, double& x, double& invT, double& rsqT) {
   if (T < tcut) {
-    ti = floor_nonneg(T);
-    x = fma(2.0, T, -(double)(2 * ti + 1));
+    ti = floor_nonneg((double)RYS_SUB * T);
+    x = fma(2.0 * RYS_SUB, T, -(double)(2 * ti + 1));
     invT = 0.0;
     rsqT = 0.0;
   } else {
@@ -65,9 +68,9 @@ __device__ __forceinline__ void rys_root(const double* __restrict__ coef, const 
                                          const double* __restrict__ aw, int N, int ti, double x,
                                          double invT, double rsqT, int n, double& u, double& w) {
   if (ti >= 0) {
-    const double* c = coef + ((size_t)ti * N + n) * 24;
-    u = horner12(c, x);
-    w = horner12(c + 12, x);
+    const double* c = coef + ((size_t)ti * N + n) * (2 * (RYS_DEG + 1));
+    u = horner_rys(c, x);
+    w = horner_rys(c + RYS_DEG + 1, x);
   } else {
     u = __ldg(au + n) * invT;
     w = __ldg(aw + n) * rsqT;

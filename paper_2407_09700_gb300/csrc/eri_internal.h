@@ -57,7 +57,19 @@ struct ClassDesc {
   int team_doubles_f32;  // shared-memory doubles per team (FP32 recurrences)
   int hrr_doubles;       // size of one HRR ping-pong buffer (doubles)
   long long scratch_per_team;  // global scratch doubles per team
-  const uint32_t* outidx;      // [nout] packed 2D offsets ix | iy << 8 | iz << 16
+  const uint32_t* outidx;      // [nout] packed 2D offsets ix | iy << 8 | iz << 16 (xy = 0), or
+                               // product index within the pass | iz << 16 (xy = 1)
+  // Shared I_x I_y products (team kernels, xy = 1): the [e0|f0] values are ordered by their
+  // (e_x, e_y, f_x, f_y) product; each pass forms its products once per (primitive, root)
+  // in shared memory and every value is one FMA with I_z.
+  int xy;                      // 1: products path
+  int xymax;                   // most products in one pass
+  int ncomb;                   // distinct products of the class
+  int xysum;                   // products formed per (primitive, root) over all passes
+  const uint32_t* xytab;       // [ncomb] ix | iy << 8
+  const uint32_t* dst;         // [nout] E0 position (e * nf + f) of each ordered value
+  const uint32_t* passinfo;    // [npass][2] first product, products in the pass
+  int xytab_off, dst_off, pass_off;   // offsets of the three tables after outidx (host)
 };
 
 enum { KMODE_JK = 0, KMODE_BLOCK = 1, KMODE_SCHWARZ = 2 };
@@ -161,7 +173,7 @@ extern "C" {
 #endif
 int erik_upload_cart_tables(void);
 int erik_team_config(int ts, int* threads_per_block, int* max_g);
-int erik_blocks_per_sm(int ts, int fp32, int smem_bytes, int* out);
+int erik_blocks_per_sm(int ts, int fp32, int xy, int smem_bytes, int* out);
 int erik_launch_class(int ts, int fp32, const struct KernelArgs* a, int grid, int smem_bytes, void* stream);
 int erik_launch_compact(const struct KernelArgs* a, unsigned* tlist, unsigned long long cap,
                         unsigned long long* counts, unsigned* tiles, int mixed, void* stream);

@@ -2,7 +2,7 @@
 // (arXiv 2407.09700, Secs. 2-3), written for sm_103a.
 //
 // One launch per angular-momentum class (la lb | lc ld).  A "team" of TS threads
-// owns one contracted shell quartet at a time (TS = 1, 8 or 32); a warp holds
+// owns one contracted shell quartet at a time (TS = 1, 2, 4, 8 or 32); a warp holds
 // 32/TS teams and all control flow is warp-uniform, so the FP64 pipe never runs a
 // warp instruction for a team that has left the loop.  Per quartet:
 //   1. loop over primitive quartets in batches of bp:
@@ -32,6 +32,7 @@
 // ordered writes.  Keeping the order keeps neighbouring tasks on the same bra pair and on
 // ket pairs of equal contraction depth, so a warp's primitive loops stay uniform.
 #define CTILE 1024
+#define XQ 12      // product indices a lane keeps in registers (products path)
 __device__ __forceinline__ int task_category(const KernelArgs& a, long long task, int mixed) {
   if (task >= a.ntask) return 0;
   int ib, ik;
@@ -177,7 +178,7 @@ __global__ void compact_write_batched_kernel(const KernelArgs a, int mixed, cons
 // recurrences, Eq. 1's products and the Eq. 5 contraction in FP32; T and the Rys roots /
 // weights in FP64, rounded at the recurrence input; the transfer relations, digestion and
 // the J / K accumulation in FP64).
-template <int TS, typename R>
+template <int TS, typename R, bool XY>
 __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : 2)) eri_class_kernel(const KernelArgs a) {
   extern __shared__ double smem[];
   typedef typename PairOf<R>::type PP;
@@ -205,6 +206,7 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : 2)) eri_class_kernel(const
     sr.es = 1;
   }
   const int S_2D = bp * NPR;                         // R offset of the 2D tables
+  R* xyb = XY ? &sr[S_2D + bp * 3 * N * nI] : nullptr;   // product buffers (xy classes)
   // contracted [e0|f0] and the transfer relations are FP64 in both paths: the FP32 path
   // hands its contracted values over before the transfer, whose cancellations grow with |A-B|
   double* scr = a.scratch + gteam * c.scratch_per_team;
@@ -275,6 +277,18 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : 2)) eri_class_kernel(const
         acc[k] = R(0);
       }
       const int kcnt = min(GSLOTS, (c.nout - o0 + TS - 1) / TS);   // uniform
+      const uint32_t* xyt = nullptr;                 // products of this pass (xy classes)
+      int ncp = 0;
+      uint32_t xq[XY ? XQ : 1];                      // this lane's first product indices
+      if (XY) {
+        xyt = c.xytab + __ldg(c.passinfo + 2 * pass);
+        ncp = (int)__ldg(c.passinfo + 2 * pass + 1);
+#pragma unroll
+        for (int i = 0; i < XQ; ++i) {
+          const int t = tl + i * TS;
+          xq[i] = (t < ncp) ? __ldg(xyt + t) : 0u;
+        }
+      }
 
       for (int q0 = 0; q0 < maxq; q0 += bp) {
         const int nbt = min(bp, nq - q0);            // this team's primitives in the batch (may be <= 0)
@@ -349,18 +363,61 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : 2)) eri_class_kernel(const
         }
         __syncwarp();
         // ---- c. assembly of [e0|f0] (Eq. 1) and contraction (Eq. 5) in registers
-        for (int j = 0; j < bp; ++j) {
-          if (j < nbt) {
-            for (int n = 0; n < N; ++n) {
-              const int gx = S_2D + ((j * 3 + 0) * N + n) * nI;
-              const int gy = gx + N * nI;
-              const int gz = gy + N * nI;
+        if (XY) {
+          // products path: per (primitive, root) step the team forms this pass's distinct
+          // I_x I_y products once, then each value is one FMA with I_z.  Software-pipelined
+          // over steps: the products of step s+1 (buffer (s+1)&1) are formed while the FMAs
+          // of step s read buffer s&1, with one warp synchronisation per step.  Steps of a
+          // team past its primitive count compute on stale (in-bounds) table entries and
+          // leave the accumulators unchanged.
+          const int nsteps = warp_max(nbt) * N;
+          auto form = [&](int st) {
+            const int jj = st / N, nn = st - (st / N) * N;
+            const int gx = S_2D + ((jj * 3 + 0) * N + nn) * nI;
+            const int gy = gx + N * nI;
+            R* buf = xyb + (st & 1) * c.xymax;
 #pragma unroll
-              for (int k = 0; k < GSLOTS; ++k) {
-                if (k < kcnt) {
-                  const uint32_t p = (TS == 1) ? __ldg(c.outidx + o0 + k) : pkd[k];
-                  const R v = sr[gx + (int)(p & 0xffu)] * sr[gy + (int)((p >> 8) & 0xffu)];
-                  acc[k] = fma(v, sr[gz + (int)((p >> 16) & 0xffu)], acc[k]);
+            for (int i = 0; i < XQ; ++i) {
+              const int t = tl + i * TS;
+              if (t < ncp) buf[t] = sr[gx + (int)(xq[i] & 0xffu)] * sr[gy + (int)((xq[i] >> 8) & 0xffu)];
+            }
+            for (int t = tl + XQ * TS; t < ncp; t += TS) {
+              const uint32_t q = __ldg(xyt + t);
+              buf[t] = sr[gx + (int)(q & 0xffu)] * sr[gy + (int)((q >> 8) & 0xffu)];
+            }
+          };
+          if (nsteps > 0) form(0);
+          __syncwarp();
+          for (int st = 0; st < nsteps; ++st) {
+            if (st + 1 < nsteps) form(st + 1);
+            const int jj = st / N, nn = st - (st / N) * N;
+            const bool jv = jj < nbt;
+            const int gz = S_2D + ((jj * 3 + 2) * N + nn) * nI;
+            const R* buf = xyb + (st & 1) * c.xymax;
+#pragma unroll
+            for (int k = 0; k < GSLOTS; ++k) {
+              if (k < kcnt) {
+                const uint32_t p = pkd[k];
+                const R v = fma(buf[(int)(p & 0xffffu)], sr[gz + (int)((p >> 16) & 0xffu)], acc[k]);
+                acc[k] = jv ? v : acc[k];
+              }
+            }
+            __syncwarp();
+          }
+        } else {
+          for (int j = 0; j < bp; ++j) {
+            if (j < nbt) {
+              for (int n = 0; n < N; ++n) {
+                const int gx = S_2D + ((j * 3 + 0) * N + n) * nI;
+                const int gy = gx + N * nI;
+                const int gz = gy + N * nI;
+#pragma unroll
+                for (int k = 0; k < GSLOTS; ++k) {
+                  if (k < kcnt) {
+                    const uint32_t p = (TS == 1) ? __ldg(c.outidx + o0 + k) : pkd[k];
+                    const R v = sr[gx + (int)(p & 0xffu)] * sr[gy + (int)((p >> 8) & 0xffu)];
+                    acc[k] = fma(v, sr[gz + (int)((p >> 16) & 0xffu)], acc[k]);
+                  }
                 }
               }
             }
@@ -368,12 +425,12 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : 2)) eri_class_kernel(const
         }
         __syncwarp();
       }
-      // ---- contracted values of this pass -> team scratch
+      // ---- contracted values of this pass -> team scratch ([e][f] order)
       if (active) {
 #pragma unroll
         for (int k = 0; k < GSLOTS; ++k) {
           const int o = o0 + k * TS + tl;
-          if (k < kcnt && o < c.nout) E0[o] = (double)acc[k];
+          if (k < kcnt && o < c.nout) E0[XY ? (int)__ldg(c.dst + o) : o] = (double)acc[k];
         }
       }
     }
@@ -469,51 +526,76 @@ extern "C" int erik_upload_cart_tables(void) {
 extern "C" int erik_team_config(int ts, int* threads_per_block, int* max_g) {
   *threads_per_block = TPB;
   *max_g = GSLOTS;
-  return (ts == 1 || ts == 8 || ts == 32) ? 0 : 1;
+  return (ts == 1 || ts == 2 || ts == 4 || ts == 8 || ts == 32) ? 0 : 1;
 }
 
-static const void* class_kernel_ptr(int ts, int fp32) {
+static const void* class_kernel_ptr(int ts, int fp32, int xy) {
   if (fp32) {
-    switch (ts) {
-      case 1: return (const void*)eri_class_kernel<1, float>;
-      case 8: return (const void*)eri_class_kernel<8, float>;
-      case 32: return (const void*)eri_class_kernel<32, float>;
+    switch (ts * 2 + (xy ? 1 : 0)) {
+      case 2: return (const void*)eri_class_kernel<1, float, false>;
+      case 4: return (const void*)eri_class_kernel<2, float, false>;
+      case 5: return (const void*)eri_class_kernel<2, float, true>;
+      case 8: return (const void*)eri_class_kernel<4, float, false>;
+      case 9: return (const void*)eri_class_kernel<4, float, true>;
+      case 16: return (const void*)eri_class_kernel<8, float, false>;
+      case 17: return (const void*)eri_class_kernel<8, float, true>;
+      case 64: return (const void*)eri_class_kernel<32, float, false>;
+      case 65: return (const void*)eri_class_kernel<32, float, true>;
     }
   } else {
-    switch (ts) {
-      case 1: return (const void*)eri_class_kernel<1, double>;
-      case 8: return (const void*)eri_class_kernel<8, double>;
-      case 32: return (const void*)eri_class_kernel<32, double>;
+    switch (ts * 2 + (xy ? 1 : 0)) {
+      case 2: return (const void*)eri_class_kernel<1, double, false>;
+      case 4: return (const void*)eri_class_kernel<2, double, false>;
+      case 5: return (const void*)eri_class_kernel<2, double, true>;
+      case 8: return (const void*)eri_class_kernel<4, double, false>;
+      case 9: return (const void*)eri_class_kernel<4, double, true>;
+      case 16: return (const void*)eri_class_kernel<8, double, false>;
+      case 17: return (const void*)eri_class_kernel<8, double, true>;
+      case 64: return (const void*)eri_class_kernel<32, double, false>;
+      case 65: return (const void*)eri_class_kernel<32, double, true>;
     }
   }
   return nullptr;
 }
 
-extern "C" int erik_blocks_per_sm(int ts, int fp32, int smem_bytes, int* out) {
-  const void* k = class_kernel_ptr(ts, fp32);
+extern "C" int erik_blocks_per_sm(int ts, int fp32, int xy, int smem_bytes, int* out) {
+  const void* k = class_kernel_ptr(ts, fp32, xy);
   if (!k) return (int)cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   if (e != cudaSuccess) return (int)e;
   return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k, TPB, smem_bytes);
 }
 
+// The products path (KernelArgs::c.xy) selects its own instantiation.
 extern "C" int erik_launch_class(int ts, int fp32, const KernelArgs* a, int grid, int smem_bytes, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
+  const bool xy = a->c.xy != 0;
+  if (xy && ts == 1) return (int)cudaErrorInvalidValue;
+#define CLASS_LAUNCH(T, R)                                                                     \
+  if (xy)                                                                                      \
+    eri_class_kernel<T, R, (T > 1)><<<grid, TPB, smem_bytes, s>>>(*a);                        \
+  else                                                                                         \
+    eri_class_kernel<T, R, false><<<grid, TPB, smem_bytes, s>>>(*a);
   if (fp32) {
     switch (ts) {
-      case 1: eri_class_kernel<1, float><<<grid, TPB, smem_bytes, s>>>(*a); break;
-      case 8: eri_class_kernel<8, float><<<grid, TPB, smem_bytes, s>>>(*a); break;
-      case 32: eri_class_kernel<32, float><<<grid, TPB, smem_bytes, s>>>(*a); break;
+      case 1: CLASS_LAUNCH(1, float) break;
+      case 2: CLASS_LAUNCH(2, float) break;
+      case 4: CLASS_LAUNCH(4, float) break;
+      case 8: CLASS_LAUNCH(8, float) break;
+      case 32: CLASS_LAUNCH(32, float) break;
       default: return (int)cudaErrorInvalidValue;
     }
   } else {
     switch (ts) {
-      case 1: eri_class_kernel<1, double><<<grid, TPB, smem_bytes, s>>>(*a); break;
-      case 8: eri_class_kernel<8, double><<<grid, TPB, smem_bytes, s>>>(*a); break;
-      case 32: eri_class_kernel<32, double><<<grid, TPB, smem_bytes, s>>>(*a); break;
+      case 1: CLASS_LAUNCH(1, double) break;
+      case 2: CLASS_LAUNCH(2, double) break;
+      case 4: CLASS_LAUNCH(4, double) break;
+      case 8: CLASS_LAUNCH(8, double) break;
+      case 32: CLASS_LAUNCH(32, double) break;
       default: return (int)cudaErrorInvalidValue;
     }
   }
+#undef CLASS_LAUNCH
   return (int)cudaGetLastError();
 }
 

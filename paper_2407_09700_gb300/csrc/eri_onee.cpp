@@ -37,8 +37,8 @@ inline void cart_lmn(int l, int pos, int v[3]) {
 // Host evaluation of the Rys table: N roots u and weights w at T.
 void rys_host(int N, double T, double* u, double* w) {
   if (T < (double)RYS_TCUT[N]) {
-    const int ti = (int)T;
-    const double x = 2.0 * (T - ti) - 1.0;
+    const int ti = (int)(RYS_SUB * T);
+    const double x = 2.0 * (RYS_SUB * T - ti) - 1.0;
     const double* c = RYS_COEF + RYS_COEF_OFFSET[N] + (size_t)ti * N * 2 * (RYS_DEG + 1);
     for (int n = 0; n < N; ++n) {
       const double* cu = c + n * 2 * (RYS_DEG + 1);

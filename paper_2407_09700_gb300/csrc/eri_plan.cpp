@@ -13,6 +13,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -101,8 +102,51 @@ int choose_ts(int nout) {
   return 32;
 }
 
-// Fill the static part of a class descriptor (no device pointers).
+// Shared-memory doubles per team for the batch tables: about 98 KB per 128-thread block,
+// so two blocks fit on an SM.
+int team_budget(int ts) { return ts == 2 ? 192 : ts == 4 ? 384 : ts == 8 ? 768 : 3072; }
+
+// Per-class overrides of the team size and the products path: "la lb lc ld ts xy" entries
+// separated by ';' in ERI_CLASS_CONFIG (xy -1 = automatic), read once per process.  For
+// tuning the choice on new hardware.
+struct ClassTune { int ts = -1, xy = -1; };
+ClassTune class_tune(int la, int lb, int lc, int ld) {
+  static std::vector<std::vector<int>> table;
+  static bool read = false;
+  if (!read) {
+    read = true;
+    if (const char* env = std::getenv("ERI_CLASS_CONFIG")) {
+      std::string str(env);
+      size_t pos = 0;
+      while (pos < str.size()) {
+        size_t end = str.find(';', pos);
+        if (end == std::string::npos) end = str.size();
+        std::vector<int> v(6, -1);
+        if (sscanf(str.substr(pos, end - pos).c_str(), "%d %d %d %d %d %d", &v[0], &v[1], &v[2], &v[3], &v[4], &v[5]) >= 5)
+          table.push_back(v);
+        pos = end + 1;
+      }
+    }
+  }
+  ClassTune t;
+  // team sizes measured fastest on GB300 for the s/p/d classes of contracted 6-31G(d)-like
+  // shells (per-class CUDA-event times of the FP64 build, 1/2/4/8/32 lanes compared)
+  static const int measured[][5] = {{2, 1, 1, 0, 2}, {2, 2, 1, 0, 4}, {2, 0, 2, 0, 4}, {1, 1, 1, 1, 4}, {2, 2, 2, 1, 8}};
+  for (const auto& m : measured)
+    if (m[0] == la && m[1] == lb && m[2] == lc && m[3] == ld) t.ts = m[4];
+  for (const auto& v : table)
+    if (v[0] == la && v[1] == lb && v[2] == lc && v[3] == ld) {
+      if (v[4] == 1 || v[4] == 2 || v[4] == 4 || v[4] == 8 || v[4] == 32) t.ts = v[4];
+      t.xy = v[5];
+    }
+  return t;
+}
+
+// Fill the static part of a class descriptor (no device pointers).  idx receives the
+// class's u32 tables: outidx [nout], then (xy classes) xytab [ncomb], dst [nout] and
+// passinfo [npass][2].
 void make_class(int la, int lb, int lc, int ld, ClassDesc* c, int* ts, std::vector<uint32_t>* idx) {
+  memset(c, 0, sizeof(*c));
   c->la = la; c->lb = lb; c->lc = lc; c->ld = ld;
   c->nroots = (la + lb + lc + ld) / 2 + 1;
   c->Le = la + lb;
@@ -117,26 +161,107 @@ void make_class(int la, int lb, int lc, int ld, ClassDesc* c, int* ts, std::vect
   const CartTab& ct = cart();
   idx->clear();
   const int L1 = c->Lf + 1;
-  for (int ie = 0; ie < c->ne; ++ie)
-    for (int jf = 0; jf < c->nf; ++jf) {
-      const int e = c->e_base + ie, f = c->f_base + jf;
-      const uint32_t ix = ct.lx[e] * L1 + ct.lx[f];
-      const uint32_t iy = ct.ly[e] * L1 + ct.ly[f];
-      const uint32_t iz = ct.lz[e] * L1 + ct.lz[f];
-      idx->push_back(ix | (iy << 8) | (iz << 16));
+  const ClassTune tune = class_tune(la, lb, lc, ld);
+  *ts = tune.ts > 0 ? tune.ts : choose_ts(c->nout);
+  const int per_pass = *ts * 32;
+  c->npass = (c->nout + per_pass - 1) / per_pass;
+
+  // distinct (e_x, e_y) over the e range and (f_x, f_y) over the f range
+  std::vector<int> eid(c->ne), fid(c->nf);
+  std::vector<int> erep, frep;
+  {
+    std::vector<int> seen((c->Le + 1) * (c->Le + 1), -1);
+    for (int ie = 0; ie < c->ne; ++ie) {
+      const int e = c->e_base + ie, key = ct.lx[e] * (c->Le + 1) + ct.ly[e];
+      if (seen[key] < 0) { seen[key] = (int)erep.size(); erep.push_back(e); }
+      eid[ie] = seen[key];
     }
-  *ts = choose_ts(c->nout);
-  c->npass = (c->nout + *ts * 32 - 1) / (*ts * 32);
-  // per primitive quartet: 4 doubles (table lookup) + 18 recurrence-type scalars + three 2D tables
+  }
+  {
+    std::vector<int> seen((c->Lf + 1) * (c->Lf + 1), -1);
+    for (int jf = 0; jf < c->nf; ++jf) {
+      const int f = c->f_base + jf, key = ct.lx[f] * (c->Lf + 1) + ct.ly[f];
+      if (seen[key] < 0) { seen[key] = (int)frep.size(); frep.push_back(f); }
+      fid[jf] = seen[key];
+    }
+  }
+  const int nec = (int)erep.size(), nfc = (int)frep.size();
+  c->ncomb = nec * nfc;
+  // Values ordered by their I_x I_y product; per pass the first product and the count.
+  struct O { int comb, ie, jf; };
+  std::vector<O> ord;
+  for (int ie = 0; ie < c->ne; ++ie)
+    for (int jf = 0; jf < c->nf; ++jf) ord.push_back({eid[ie] * nfc + fid[jf], ie, jf});
+  std::stable_sort(ord.begin(), ord.end(), [](const O& x, const O& y) { return x.comb < y.comb; });
+  std::vector<uint32_t> pinfo(2 * c->npass);
+  int xymax = 0, xysum = 0;
+  for (int p = 0; p < c->npass; ++p) {
+    const int o0 = p * per_pass, o1 = std::min(c->nout, o0 + per_pass) - 1;
+    pinfo[2 * p] = (uint32_t)ord[o0].comb;
+    pinfo[2 * p + 1] = (uint32_t)(ord[o1].comb - ord[o0].comb + 1);
+    xymax = std::max(xymax, (int)pinfo[2 * p + 1]);
+    xysum += (int)pinfo[2 * p + 1];
+  }
+  // The products path pays a warp synchronisation and a shared-memory round trip per
+  // (primitive, root) step and shrinks the primitive batch; measured on GB300 it wins when
+  // a lane accumulates at least 20 values per pass, the products save at least a fifth of
+  // the multiplies, and the smaller batch costs no more root-phase lane iterations per
+  // primitive quartet (ceil(bp N / TS) / bp) than the larger one.
+  {
+    const int per_prim0 = 4 + 18 + 3 * c->nroots * c->nI;
+    const int kcnt = std::min(32, (c->nout + *ts - 1) / *ts);
+    const int bp_off = std::max(1, std::min(32, team_budget(*ts) / per_prim0));
+    const int bp_on = std::max(1, std::min(32, (team_budget(*ts) - 2 * xymax) / per_prim0));
+    auto iters = [&](int bp) { return (double)((bp * c->nroots + *ts - 1) / *ts) / bp; };
+    const bool fills = iters(bp_on) <= 1.1 * iters(bp_off);
+    c->xy = (*ts > 1 && kcnt >= 20 && 5 * xysum <= 4 * c->nout && fills) ? 1 : 0;
+    if (*ts > 1 && tune.xy >= 0) c->xy = tune.xy ? 1 : 0;
+  }
+  if (!c->xy) {
+    for (int ie = 0; ie < c->ne; ++ie)
+      for (int jf = 0; jf < c->nf; ++jf) {
+        const int e = c->e_base + ie, f = c->f_base + jf;
+        const uint32_t ix = ct.lx[e] * L1 + ct.lx[f];
+        const uint32_t iy = ct.ly[e] * L1 + ct.ly[f];
+        const uint32_t iz = ct.lz[e] * L1 + ct.lz[f];
+        idx->push_back(ix | (iy << 8) | (iz << 16));
+      }
+  } else {
+    c->xymax = xymax;
+    c->xysum = xysum;
+    std::vector<uint32_t> outi(c->nout), dst(c->nout);
+    for (int p = 0; p < c->npass; ++p) {
+      const int o0 = p * per_pass, o1 = std::min(c->nout, o0 + per_pass) - 1;
+      for (int o = o0; o <= o1; ++o) {
+        const int e = c->e_base + ord[o].ie, f = c->f_base + ord[o].jf;
+        const uint32_t iz = ct.lz[e] * L1 + ct.lz[f];
+        outi[o] = (uint32_t)(ord[o].comb - (int)pinfo[2 * p]) | (iz << 16);
+        dst[o] = (uint32_t)(ord[o].ie * c->nf + ord[o].jf);
+      }
+    }
+    idx->insert(idx->end(), outi.begin(), outi.end());
+    c->xytab_off = (int)idx->size();
+    for (int a = 0; a < nec; ++a)
+      for (int b = 0; b < nfc; ++b) {
+        const int e = erep[a], f = frep[b];
+        idx->push_back((uint32_t)(ct.lx[e] * L1 + ct.lx[f]) | ((uint32_t)(ct.ly[e] * L1 + ct.ly[f]) << 8));
+      }
+    c->dst_off = (int)idx->size();
+    idx->insert(idx->end(), dst.begin(), dst.end());
+    c->pass_off = (int)idx->size();
+    idx->insert(idx->end(), pinfo.begin(), pinfo.end());
+  }
+  // per primitive quartet: 4 doubles (table lookup) + 18 recurrence-type scalars + three 2D
+  // tables; the products path adds two product buffers per team
   const int per_prim = 4 + 18 + 3 * c->nroots * c->nI;
+  const int xybuf = c->xy ? 2 * c->xymax : 0;
   if (*ts == 1) {
     c->bp = 1;
   } else {
-    const int budget = (*ts == 8) ? 768 : 3072;
-    c->bp = std::max(1, std::min(32, budget / per_prim));
+    c->bp = std::max(1, std::min(32, (team_budget(*ts) - xybuf) / per_prim));
   }
-  c->team_doubles = c->bp * per_prim;
-  c->team_doubles_f32 = c->bp * 4 + (c->bp * (18 + 3 * c->nroots * c->nI) + 1) / 2;
+  c->team_doubles = c->bp * per_prim + xybuf;
+  c->team_doubles_f32 = c->bp * 4 + (c->bp * (18 + 3 * c->nroots * c->nI) + xybuf + 1) / 2;
   // HRR ping-pong size: max level size of the bra (vector nf) and ket (vector nab) passes
   long long m = 1;
   for (int k = 1; k <= lb; ++k) {
@@ -192,8 +317,7 @@ void make_grad_class(int la, int lb, int lc, int ld, GradDesc* g, int* ts, std::
   if (*ts == 1) {
     g->bp = 1;
   } else {
-    const int budget = (*ts == 8) ? 768 : 3072;
-    g->bp = std::max(1, std::min(32, budget / per_prim));
+    g->bp = std::max(1, std::min(32, team_budget(*ts) / per_prim));
   }
   g->team_doubles = g->bp * per_prim;
   const int nabcd = g->na * g->nb * g->nc * g->nd;
@@ -248,7 +372,15 @@ eri_status device_init(int dev, DeviceState** out) {
     CUDA_TRY(cudaMalloc(&s.outidx, sizeof(uint32_t) * all.size()));
     CUDA_TRY(cudaMemcpy(s.outidx, all.data(), sizeof(uint32_t) * all.size(), cudaMemcpyHostToDevice));
     for (int X = 0; X < ERI_NPAIRTYPE; ++X)
-      for (int Y = 0; Y < ERI_NPAIRTYPE; ++Y) s.classes[X][Y].outidx = s.outidx + offs[X][Y];
+      for (int Y = 0; Y < ERI_NPAIRTYPE; ++Y) {
+        ClassDesc& cd = s.classes[X][Y];
+        cd.outidx = s.outidx + offs[X][Y];
+        if (cd.xy) {
+          cd.xytab = cd.outidx + cd.xytab_off;
+          cd.dst = cd.outidx + cd.dst_off;
+          cd.passinfo = cd.outidx + cd.pass_off;
+        }
+      }
     all.clear();
     for (int X = 0; X < ERI_NPAIRTYPE; ++X)
       for (int Y = 0; Y < ERI_NPAIRTYPE; ++Y) {
@@ -281,7 +413,7 @@ void class_model_flops2(const ClassDesc& c, int nD, int want, int fp32, double* 
   const int N = c.nroots, Le = c.Le, Lf = c.Lf;
   const double t_setup = 1 + 4 + 3 + 8 + 3;            // s, rsqrt, PQ, T, table lookup (FP64)
   const double r_setup = 1 + 2 + 6 + 1 + 2 + 2;        // r^2, rz, re, scaled PQ, hs, hz*rz, he*re, Theta
-  const double horner = 2 * 22.0;
+  const double horner = 2.0 * 2.0 * RYS_DEG;             // two Horner sums of RYS_DEG FMAs
   const double coef = 1 + 2 + 2 + 1 + 6 + 6;
   double mult = 0.0, vrr = 0.0;                        // running multiples; three axes
   if (Le >= 1) vrr += 1;                               // z: C00 * I0z
@@ -294,7 +426,10 @@ void class_model_flops2(const ClassDesc& c, int nD, int want, int fp32, double* 
     vrr += Le * (3 * 3.0 + 3 * 5.0 * (Lf - 1));        // rows 1..Le
     mult += Le * (Lf - 1) + Le;
   }
-  const double rec = N * (coef + mult + vrr) + 3.0 * N * c.nout;
+  // Eq. 1 products: a multiply and an FMA per value and root, or (products path) one
+  // multiply per shared product and an FMA per value
+  const double asm_ops = c.xy ? (double)c.xysum + 2.0 * c.nout : 3.0 * c.nout;
+  const double rec = N * (coef + mult + vrr) + N * asm_ops;
   double hrr = 0.0;
   for (int k = 1; k <= c.lb; ++k)
     hrr += 2.0 * (cart_below(c.la + c.lb - k + 1) - cart_below(c.la)) * ncart(k) * c.nf;
@@ -440,7 +575,7 @@ eri_status launch_shape(eri_plan* p, int X, int Y, int fp32, long long nteams_ne
   *smem = (int)(sizeof(double) * (size_t)(fp32 ? c.team_doubles_f32 : c.team_doubles) * teams_per_block);
   if (*smem > 200 * 1024) return fail(ERI_ERR_ARG, "class (%d%d|%d%d) needs %d bytes of shared memory", c.la, c.lb, c.lc, c.ld, *smem);
   int bps = 0;
-  CUDA_TRY(erik_blocks_per_sm(ts, fp32, *smem, &bps));
+  CUDA_TRY(erik_blocks_per_sm(ts, fp32, c.xy, *smem, &bps));
   if (bps < 1) bps = 1;
   long long full = (long long)p->dev->sms * bps;
   long long need = (nteams_needed + teams_per_block - 1) / teams_per_block;

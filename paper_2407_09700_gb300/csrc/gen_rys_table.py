@@ -12,9 +12,11 @@ are the Boys functions F_k(T).  For each N = 1..9 this script
      "Orthogonal Polynomials: Computation and Approximation", 2004, Sec. 2.1.7),
      then nodes and weights from the Jacobi matrix (Golub & Welsch, Math.
      Comp. 23, 221 (1969));
-  2. interpolates every u_n(T) and w_n(T) on unit intervals [i, i+1) of T by a
-     degree-11 Chebyshev interpolant, re-expanded in powers of
-     x = 2 (T - i) - 1 so the device evaluates it by Horner's rule;
+  2. interpolates every u_n(T) and w_n(T) on intervals [i/SUB, (i+1)/SUB) of T by a
+     degree-DEG Chebyshev interpolant, re-expanded in powers of
+     x = 2 (SUB T - i) - 1 so the device evaluates it by Horner's rule (SUB = 4,
+     DEG = 7: 5e-15 worst relative error for 8 FMAs per value, against 12 FMAs per value
+     for degree 11 on unit intervals);
   3. above a cutoff T_N uses the large-T limit u_n = v_n / T,
      w_n = W_n / (2 sqrt(T)), with (v_n, W_n) the N-point generalised
      Gauss-Laguerre rule for v^(-1/2) exp(-v) on [0, inf); T_N is the first
@@ -36,7 +38,8 @@ import mpmath as mp
 
 DPS = 60
 NMAX = 9
-DEG = 11            # polynomial degree on each unit interval
+DEG = 7             # polynomial degree on each interval
+SUB = 4             # intervals per unit of T
 ASYM_TOL = mp.mpf("2e-17")
 
 
@@ -155,7 +158,7 @@ def fit_interval(args):
     _setup()
     d = DEG
     xs = [mp.cos(mp.pi * (k + mp.mpf(1) / 2) / (d + 1)) for k in range(d + 1)]
-    vals = [rys_exact(N, i + (x + 1) / 2) for x in xs]
+    vals = [rys_exact(N, (i + (x + 1) / 2) / SUB) for x in xs]
     coefs = []          # [n][0=u,1=w][d+1] ascending powers, float64
     for n in range(N):
         both = []
@@ -169,7 +172,7 @@ def fit_interval(args):
     # check at interior points, float64 Horner against the exact rule
     worst_u = worst_w = 0.0
     for x in (-0.987, -0.55, -0.11, 0.23, 0.71, 0.995):
-        u, w = rys_exact(N, i + (mp.mpf(x) + 1) / 2)
+        u, w = rys_exact(N, (i + (mp.mpf(x) + 1) / 2) / SUB)
         for n in range(N):
             eu = abs(horner64(coefs[n][0], x) - float(u[n])) / float(u[n])
             ew = abs(horner64(coefs[n][1], x) - float(w[n])) / float(w[n])
@@ -192,7 +195,7 @@ def main(out_path):
     _setup()
     with mproc.get_context("spawn").Pool(os.cpu_count()) as pool:
         cut = sorted(pool.map(cutoff_job, range(1, NMAX + 1)))
-        jobs = [(N, i) for N, T, _, _ in cut for i in range(T)]
+        jobs = [(N, i) for N, T, _, _ in cut for i in range(T * SUB)]
         res = pool.map(fit_interval, jobs, chunksize=4)
     res.sort(key=lambda r: (r[0], r[1]))
     tmax = {N: T for N, T, _, _ in cut}
@@ -225,8 +228,8 @@ def main(out_path):
             name, ", ".join(str(table[N]) for N in range(1, NMAX + 1)))
 
     head = ["// Generated by gen_rys_table.py -- do not edit.",
-            "// Rys roots u_n = t_n^2 and weights w_n (sum_n w_n = F_0(T)) for N = 1..9 on unit",
-            "// intervals of T: degree-%d polynomials in x = 2 (T - floor T) - 1, highest power first," % DEG,
+            "// Rys roots u_n = t_n^2 and weights w_n (sum_n w_n = F_0(T)) for N = 1..9 on intervals",
+            "// [i/%d, (i+1)/%d) of T: degree-%d polynomials in x = 2 (%d T - i) - 1, highest power first," % (SUB, SUB, DEG, SUB),
             "// laid out [N][interval][root][u coefs, w coefs].  Above RYS_TCUT[N]:",
             "// u_n = RYS_ASYM_U[n] / T, w_n = RYS_ASYM_W[n] / sqrt(T).",
             "// Worst relative error seen at interior test points (float64 Horner):"]
@@ -234,6 +237,7 @@ def main(out_path):
         head.append("//   N=%d  T_cut=%3d  u %.2e  w %.2e" % (N, tmax[N], worst[N][0], worst[N][1]))
     text = "\n".join(head) + "\n"
     text += '#include "rys_table.h"\n\n'
+    text += "static_assert(RYS_DEG == %d && RYS_SUB == %d, \"rys_table.h does not match the table\");\n\n" % (DEG, SUB)
     text += ints("RYS_TCUT", tmax) + ints("RYS_COEF_OFFSET", offsets) + ints("RYS_ASYM_OFFSET", asym_off)
     text += "extern \"C\" const int RYS_NCOEF = %d;\n\n" % len(flat)
     text += arr("extern \"C\" const double RYS_COEF", flat)

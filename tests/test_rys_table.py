@@ -19,7 +19,9 @@ mp = pytest.importorskip("mpmath")
 
 SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
                    "paper_2407_09700_gb300", "csrc", "rys_table.cpp")
-DEG = 11
+HDR = os.path.join(os.path.dirname(SRC), "rys_table.h")
+DEG = int(re.search(r"#define RYS_DEG (\d+)", open(HDR).read()).group(1))
+SUB = int(re.search(r"#define RYS_SUB (\d+)", open(HDR).read()).group(1))
 
 
 def _arr(text, name, conv):
@@ -45,8 +47,8 @@ def rys_eval(tab, N, T):
     if T >= tab["tcut"][N]:
         a = tab["aoff"][N]
         return tab["au"][a:a + N] / T, tab["aw"][a:a + N] / np.sqrt(T)
-    i = int(T)
-    x = 2.0 * (T - i) - 1.0
+    i = int(SUB * T)
+    x = 2.0 * (SUB * T - i) - 1.0
     base = tab["off"][N] + i * N * 2 * (DEG + 1)
     u, w = np.zeros(N), np.zeros(N)
     for r in range(N):
@@ -87,8 +89,8 @@ def test_moment_identity(table, N):
 
 
 def test_table_layout(table):
-    # contiguous blocks: interval count of N equals its cutoff, no gaps between N
+    # contiguous blocks: interval count of N is SUB times its cutoff, no gaps between N
     for N in range(1, 9):
-        assert table["off"][N + 1] - table["off"][N] == table["tcut"][N] * N * 2 * (DEG + 1)
-    assert len(table["coef"]) == table["off"][9] + table["tcut"][9] * 9 * 2 * (DEG + 1)
+        assert table["off"][N + 1] - table["off"][N] == SUB * table["tcut"][N] * N * 2 * (DEG + 1)
+    assert len(table["coef"]) == table["off"][9] + SUB * table["tcut"][9] * 9 * 2 * (DEG + 1)
     assert len(table["au"]) == sum(range(1, 10))
