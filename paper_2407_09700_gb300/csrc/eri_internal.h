@@ -57,19 +57,30 @@ struct ClassDesc {
   int team_doubles_f32;  // shared-memory doubles per team (FP32 recurrences)
   int hrr_doubles;       // size of one HRR ping-pong buffer (doubles)
   long long scratch_per_team;  // global scratch doubles per team
-  const uint32_t* outidx;      // [nout] packed 2D offsets ix | iy << 8 | iz << 16 (xy = 0), or
-                               // product index within the pass | iz << 16 (xy = 1)
-  // Shared I_x I_y products (team kernels, xy = 1): the [e0|f0] values are ordered by their
-  // (e_x, e_y, f_x, f_y) product; each pass forms its products once per (primitive, root)
-  // in shared memory and every value is one FMA with I_z.
-  int xy;                      // 1: products path
+  // Assembly of Eq. 1 by lane programs (every FP32 launch; FP64 launches with xy = 0): the
+  // values sharing an I_x I_y product form groups; every lane of a team runs the same
+  // sequence of group sizes, so slot k of a pass starts a group (one multiply) for all lanes
+  // or for none: bit k of gmask[pass].  Slot tables: outidx = ix | iy << 8 | iz << 16 |
+  // unused << 31 with E0 position dst; nslot = lanes x slots per lane (>= nout; padding
+  // slots are computed and dropped); xysum = products formed per (primitive, root).
+  int nslot, xysum;
+  const uint32_t* outidx;
+  const uint32_t* dst;
+  const uint32_t* gmask;       // [npass]
+  // Shared products path (FP64 launches with xy = 1): values ordered by their product; per
+  // pass the team forms the pass's products once per (primitive, root) in shared memory
+  // and every value is one FMA with I_z.  Own pass count, batch and team region.
+  int xy;
+  int xy_npass, bp_xy, team_doubles_xy;
   int xymax;                   // most products in one pass
+  int xysum_xy;                // products formed per (primitive, root) over all passes
+  const uint32_t* xy_outidx;   // [nout] product index within the pass | iz << 16
+  const uint32_t* xy_dst;      // [nout] E0 position
+  const uint32_t* xytab;       // [products] ix | iy << 8
+  const uint32_t* passinfo;    // [xy_npass][2] first product, products in the pass
   int ncomb;                   // distinct products of the class
-  int xysum;                   // products formed per (primitive, root) over all passes
-  const uint32_t* xytab;       // [ncomb] ix | iy << 8
-  const uint32_t* dst;         // [nout] E0 position (e * nf + f) of each ordered value
-  const uint32_t* passinfo;    // [npass][2] first product, products in the pass
-  int xytab_off, dst_off, pass_off;   // offsets of the three tables after outidx (host)
+  // offsets of the tables in the class's block of the device table (host bookkeeping)
+  int dst_off, gmask_off, xy_outidx_off, xy_dst_off, xytab_off, pass_off;
 };
 
 enum { KMODE_JK = 0, KMODE_BLOCK = 1, KMODE_SCHWARZ = 2 };

@@ -179,7 +179,7 @@ __global__ void compact_write_batched_kernel(const KernelArgs a, int mixed, cons
 // weights in FP64, rounded at the recurrence input; the transfer relations, digestion and
 // the J / K accumulation in FP64).
 template <int TS, typename R, bool XY>
-__global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : 2)) eri_class_kernel(const KernelArgs a) {
+__global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : ((sizeof(R) == 4 && !XY) ? 3 : 2))) eri_class_kernel(const KernelArgs a) {
   extern __shared__ double smem[];
   typedef typename PairOf<R>::type PP;
   constexpr int TEAMS_PER_WARP = 32 / TS;
@@ -189,7 +189,11 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : 2)) eri_class_kernel(const
   const long long gteam = (long long)blockIdx.x * (TPB / TS) + team_in_block;
   const ClassDesc& c = a.c;
   const int N = c.nroots, nI = c.nI, Le = c.Le, Lf = c.Lf;
-  const int bp = c.bp;
+  const int bp = XY ? c.bp_xy : c.bp;
+  const int npass = XY ? c.xy_npass : c.npass;
+  const int nslot = XY ? c.nout : c.nslot;
+  const uint32_t* outidx = XY ? c.xy_outidx : c.outidx;
+  const uint32_t* dsttab = XY ? c.xy_dst : c.dst;
 
   // team region: [bp][NPD] doubles, then [bp][NPR] R, then [bp][3][N][nI] R
   Smem<double> sd;
@@ -200,7 +204,7 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : 2)) eri_class_kernel(const
     sr.base = reinterpret_cast<R*>(smem + (size_t)TPB * bp * NPD) + threadIdx.x;
     sr.es = TPB;
   } else {
-    sd.base = smem + (size_t)team_in_block * (sizeof(R) == 8 ? c.team_doubles : c.team_doubles_f32);
+    sd.base = smem + (size_t)team_in_block * (XY ? c.team_doubles_xy : (sizeof(R) == 8 ? c.team_doubles : c.team_doubles_f32));
     sd.es = 1;
     sr.base = reinterpret_cast<R*>(sd.base + bp * NPD);
     sr.es = 1;
@@ -264,7 +268,7 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : 2)) eri_class_kernel(const
     }
     const int boff = active ? bra->prim_off : 0, koff = active ? ket->prim_off : 0;
 
-    for (int pass = 0; pass < c.npass; ++pass) {
+    for (int pass = 0; pass < npass; ++pass) {
       // ---- my output slots for this pass
       const int o0 = pass * TS * GSLOTS;
       uint32_t pkd[GSLOTS];
@@ -273,10 +277,11 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : 2)) eri_class_kernel(const
       for (int k = 0; k < GSLOTS; ++k) {
         const int o = o0 + k * TS + tl;
         // TS = 1: every lane has the same slots, so the index is re-read (broadcast) instead
-        if (TS > 1) pkd[k] = (o < c.nout) ? __ldg(c.outidx + o) : 0u;
+        if (TS > 1) pkd[k] = (o < nslot) ? __ldg(outidx + o) : (1u << 31);
         acc[k] = R(0);
       }
-      const int kcnt = min(GSLOTS, (c.nout - o0 + TS - 1) / TS);   // uniform
+      const int kcnt = min(GSLOTS, (nslot - o0 + TS - 1) / TS);     // uniform
+      const uint32_t gm = XY ? 0u : __ldg(c.gmask + pass);           // group starts (uniform)
       const uint32_t* xyt = nullptr;                 // products of this pass (xy classes)
       int ncp = 0;
       uint32_t xq[XY ? XQ : 1];                      // this lane's first product indices
@@ -405,17 +410,20 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : 2)) eri_class_kernel(const
             __syncwarp();
           }
         } else {
+          // lane programs: a slot that starts a group forms the group's I_x I_y product, the
+          // rest of the group reuses it; the start bits are the same for every lane
           for (int j = 0; j < bp; ++j) {
             if (j < nbt) {
               for (int n = 0; n < N; ++n) {
                 const int gx = S_2D + ((j * 3 + 0) * N + n) * nI;
                 const int gy = gx + N * nI;
                 const int gz = gy + N * nI;
+                R v = R(0);
 #pragma unroll
                 for (int k = 0; k < GSLOTS; ++k) {
                   if (k < kcnt) {
-                    const uint32_t p = (TS == 1) ? __ldg(c.outidx + o0 + k) : pkd[k];
-                    const R v = sr[gx + (int)(p & 0xffu)] * sr[gy + (int)((p >> 8) & 0xffu)];
+                    const uint32_t p = (TS == 1) ? __ldg(outidx + o0 + k) : pkd[k];
+                    if ((gm >> k) & 1u) v = sr[gx + (int)(p & 0xffu)] * sr[gy + (int)((p >> 8) & 0xffu)];
                     acc[k] = fma(v, sr[gz + (int)((p >> 16) & 0xffu)], acc[k]);
                   }
                 }
@@ -430,7 +438,10 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : 2)) eri_class_kernel(const
 #pragma unroll
         for (int k = 0; k < GSLOTS; ++k) {
           const int o = o0 + k * TS + tl;
-          if (k < kcnt && o < c.nout) E0[XY ? (int)__ldg(c.dst + o) : o] = (double)acc[k];
+          if (k < kcnt && o < nslot) {
+            const uint32_t p = (TS == 1) ? __ldg(outidx + o0 + k) : pkd[k];
+            if (XY || !(p >> 31)) E0[(int)__ldg(dsttab + o)] = (double)acc[k];
+          }
         }
       }
     }
@@ -534,13 +545,9 @@ static const void* class_kernel_ptr(int ts, int fp32, int xy) {
     switch (ts * 2 + (xy ? 1 : 0)) {
       case 2: return (const void*)eri_class_kernel<1, float, false>;
       case 4: return (const void*)eri_class_kernel<2, float, false>;
-      case 5: return (const void*)eri_class_kernel<2, float, true>;
       case 8: return (const void*)eri_class_kernel<4, float, false>;
-      case 9: return (const void*)eri_class_kernel<4, float, true>;
       case 16: return (const void*)eri_class_kernel<8, float, false>;
-      case 17: return (const void*)eri_class_kernel<8, float, true>;
       case 64: return (const void*)eri_class_kernel<32, float, false>;
-      case 65: return (const void*)eri_class_kernel<32, float, true>;
     }
   } else {
     switch (ts * 2 + (xy ? 1 : 0)) {
@@ -566,14 +573,15 @@ extern "C" int erik_blocks_per_sm(int ts, int fp32, int xy, int smem_bytes, int*
   return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k, TPB, smem_bytes);
 }
 
-// The products path (KernelArgs::c.xy) selects its own instantiation.
+// FP64 launches of classes with c.xy take the shared products instantiation; FP32 launches
+// always run lane programs.
 extern "C" int erik_launch_class(int ts, int fp32, const KernelArgs* a, int grid, int smem_bytes, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
-  const bool xy = a->c.xy != 0;
+  const bool xy = a->c.xy != 0 && !fp32;
   if (xy && ts == 1) return (int)cudaErrorInvalidValue;
 #define CLASS_LAUNCH(T, R)                                                                     \
   if (xy)                                                                                      \
-    eri_class_kernel<T, R, (T > 1)><<<grid, TPB, smem_bytes, s>>>(*a);                        \
+    eri_class_kernel<T, R, (T > 1 && sizeof(R) == 8)><<<grid, TPB, smem_bytes, s>>>(*a);      \
   else                                                                                         \
     eri_class_kernel<T, R, false><<<grid, TPB, smem_bytes, s>>>(*a);
   if (fp32) {

@@ -143,8 +143,9 @@ ClassTune class_tune(int la, int lb, int lc, int ld) {
 }
 
 // Fill the static part of a class descriptor (no device pointers).  idx receives the
-// class's u32 tables: outidx [nout], then (xy classes) xytab [ncomb], dst [nout] and
-// passinfo [npass][2].
+// class's u32 tables: lane-program outidx [nslot], dst [nslot], gmask [npass], then (xy
+// classes) the shared-products tables xy_outidx [nout], xy_dst [nout], xytab [ncomb],
+// passinfo [xy_npass][2].
 void make_class(int la, int lb, int lc, int ld, ClassDesc* c, int* ts, std::vector<uint32_t>* idx) {
   memset(c, 0, sizeof(*c));
   c->la = la; c->lb = lb; c->lc = lc; c->ld = ld;
@@ -163,8 +164,8 @@ void make_class(int la, int lb, int lc, int ld, ClassDesc* c, int* ts, std::vect
   const int L1 = c->Lf + 1;
   const ClassTune tune = class_tune(la, lb, lc, ld);
   *ts = tune.ts > 0 ? tune.ts : choose_ts(c->nout);
-  const int per_pass = *ts * 32;
-  c->npass = (c->nout + per_pass - 1) / per_pass;
+  const int T = *ts;
+  const int per_pass = T * 32;
 
   // distinct (e_x, e_y) over the e range and (f_x, f_y) over the f range
   std::vector<int> eid(c->ne), fid(c->nf);
@@ -187,81 +188,143 @@ void make_class(int la, int lb, int lc, int ld, ClassDesc* c, int* ts, std::vect
   }
   const int nec = (int)erep.size(), nfc = (int)frep.size();
   c->ncomb = nec * nfc;
-  // Values ordered by their I_x I_y product; per pass the first product and the count.
-  struct O { int comb, ie, jf; };
-  std::vector<O> ord;
-  for (int ie = 0; ie < c->ne; ++ie)
-    for (int jf = 0; jf < c->nf; ++jf) ord.push_back({eid[ie] * nfc + fid[jf], ie, jf});
-  std::stable_sort(ord.begin(), ord.end(), [](const O& x, const O& y) { return x.comb < y.comb; });
-  std::vector<uint32_t> pinfo(2 * c->npass);
-  int xymax = 0, xysum = 0;
-  for (int p = 0; p < c->npass; ++p) {
-    const int o0 = p * per_pass, o1 = std::min(c->nout, o0 + per_pass) - 1;
-    pinfo[2 * p] = (uint32_t)ord[o0].comb;
-    pinfo[2 * p + 1] = (uint32_t)(ord[o1].comb - ord[o0].comb + 1);
-    xymax = std::max(xymax, (int)pinfo[2 * p + 1]);
-    xysum += (int)pinfo[2 * p + 1];
-  }
-  // The products path pays a warp synchronisation and a shared-memory round trip per
-  // (primitive, root) step and shrinks the primitive batch; measured on GB300 it wins when
-  // a lane accumulates at least 20 values per pass, the products save at least a fifth of
-  // the multiplies, and the smaller batch costs no more root-phase lane iterations per
-  // primitive quartet (ceil(bp N / TS) / bp) than the larger one.
+  auto slot_word = [&](int ie, int jf) {
+    const int e = c->e_base + ie, f = c->f_base + jf;
+    return (uint32_t)(ct.lx[e] * L1 + ct.lx[f]) | ((uint32_t)(ct.ly[e] * L1 + ct.ly[f]) << 8) |
+           ((uint32_t)(ct.lz[e] * L1 + ct.lz[f]) << 16);
+  };
+
+  // ---- lane programs: groups of values sharing a product, split until every group size
+  // occurs a multiple of TS times (a leftover group of size s > 1 becomes s-1 and 1; a
+  // leftover of single values is padded), then dealt out so each lane gets one group of
+  // each program entry
   {
-    const int per_prim0 = 4 + 18 + 3 * c->nroots * c->nI;
-    const int kcnt = std::min(32, (c->nout + *ts - 1) / *ts);
-    const int bp_off = std::max(1, std::min(32, team_budget(*ts) / per_prim0));
-    const int bp_on = std::max(1, std::min(32, (team_budget(*ts) - 2 * xymax) / per_prim0));
-    auto iters = [&](int bp) { return (double)((bp * c->nroots + *ts - 1) / *ts) / bp; };
-    const bool fills = iters(bp_on) <= 1.1 * iters(bp_off);
-    c->xy = (*ts > 1 && kcnt >= 20 && 5 * xysum <= 4 * c->nout && fills) ? 1 : 0;
-    if (*ts > 1 && tune.xy >= 0) c->xy = tune.xy ? 1 : 0;
-  }
-  if (!c->xy) {
+    std::vector<std::vector<int>> groups(c->ncomb);
     for (int ie = 0; ie < c->ne; ++ie)
-      for (int jf = 0; jf < c->nf; ++jf) {
-        const int e = c->e_base + ie, f = c->f_base + jf;
-        const uint32_t ix = ct.lx[e] * L1 + ct.lx[f];
-        const uint32_t iy = ct.ly[e] * L1 + ct.ly[f];
-        const uint32_t iz = ct.lz[e] * L1 + ct.lz[f];
-        idx->push_back(ix | (iy << 8) | (iz << 16));
+      for (int jf = 0; jf < c->nf; ++jf) groups[eid[ie] * nfc + fid[jf]].push_back(ie * c->nf + jf);
+    int smax = 1;
+    for (const auto& g : groups) smax = std::max(smax, (int)g.size());
+    std::vector<std::vector<std::vector<int>>> bys(smax + 1);
+    for (auto& g : groups)
+      if (!g.empty()) bys[g.size()].push_back(g);
+    std::vector<std::vector<std::vector<int>>> lane(T);
+    std::vector<int> prog;
+    for (int sz = smax; sz >= 1; --sz) {
+      auto& L = bys[sz];
+      const int q = (int)L.size() / T, r = (int)L.size() % T;
+      for (int t = 0; t < q; ++t) {
+        prog.push_back(sz);
+        for (int ln = 0; ln < T; ++ln) lane[ln].push_back(L[t * T + ln]);
       }
-  } else {
-    c->xymax = xymax;
-    c->xysum = xysum;
-    std::vector<uint32_t> outi(c->nout), dst(c->nout);
-    for (int p = 0; p < c->npass; ++p) {
-      const int o0 = p * per_pass, o1 = std::min(c->nout, o0 + per_pass) - 1;
-      for (int o = o0; o <= o1; ++o) {
-        const int e = c->e_base + ord[o].ie, f = c->f_base + ord[o].jf;
-        const uint32_t iz = ct.lz[e] * L1 + ct.lz[f];
-        outi[o] = (uint32_t)(ord[o].comb - (int)pinfo[2 * p]) | (iz << 16);
-        dst[o] = (uint32_t)(ord[o].ie * c->nf + ord[o].jf);
+      if (r) {
+        if (sz > 1) {
+          for (int t = q * T; t < (int)L.size(); ++t) {
+            std::vector<int> head(L[t].begin(), L[t].end() - 1), tail(1, L[t].back());
+            bys[sz - 1].push_back(head);
+            bys[1].push_back(tail);
+          }
+        } else {
+          prog.push_back(1);
+          for (int ln = 0; ln < T; ++ln) lane[ln].push_back(ln < r ? L[q * T + ln] : std::vector<int>(1, -1));
+        }
       }
     }
+    int Ls = 0;
+    for (int sz : prog) Ls += sz;
+    c->nslot = Ls * T;
+    c->npass = (Ls + 31) / 32;
+    std::vector<uint32_t> outi(c->nslot, 1u << 31), dst(c->nslot, 0), gm(c->npass, 0);
+    std::vector<int> start(Ls, 0);
+    int k = 0;
+    for (int sz : prog) {
+      for (int m = 0; m < sz; ++m) start[k + m] = (m == 0);
+      k += sz;
+    }
+    for (int k2 = 0; k2 < Ls; k2 += 32) start[k2] = 1;        // a pass starts with a product
+    for (int k2 = 0; k2 < Ls; ++k2)
+      if (start[k2]) gm[k2 / 32] |= 1u << (k2 % 32);
+    int xys = 0;
+    for (int ln = 0; ln < T; ++ln) {
+      int kk = 0;
+      for (const auto& g : lane[ln])
+        for (size_t m = 0; m < g.size(); ++m, ++kk) {
+          const int o = (kk / 32) * per_pass + (kk % 32) * T + ln;
+          if (g[m] < 0) continue;
+          outi[o] = slot_word(g[m] / c->nf, g[m] % c->nf);
+          dst[o] = (uint32_t)g[m];
+          if (start[kk]) ++xys;
+        }
+    }
+    c->xysum = xys;
     idx->insert(idx->end(), outi.begin(), outi.end());
-    c->xytab_off = (int)idx->size();
-    for (int a = 0; a < nec; ++a)
-      for (int b = 0; b < nfc; ++b) {
-        const int e = erep[a], f = frep[b];
-        idx->push_back((uint32_t)(ct.lx[e] * L1 + ct.lx[f]) | ((uint32_t)(ct.ly[e] * L1 + ct.ly[f]) << 8));
-      }
     c->dst_off = (int)idx->size();
     idx->insert(idx->end(), dst.begin(), dst.end());
-    c->pass_off = (int)idx->size();
-    idx->insert(idx->end(), pinfo.begin(), pinfo.end());
+    c->gmask_off = (int)idx->size();
+    idx->insert(idx->end(), gm.begin(), gm.end());
   }
-  // per primitive quartet: 4 doubles (table lookup) + 18 recurrence-type scalars + three 2D
-  // tables; the products path adds two product buffers per team
+  // per primitive quartet: 4 doubles (table lookup) + 18 recurrence-type scalars + three 2D tables
   const int per_prim = 4 + 18 + 3 * c->nroots * c->nI;
-  const int xybuf = c->xy ? 2 * c->xymax : 0;
-  if (*ts == 1) {
-    c->bp = 1;
-  } else {
-    c->bp = std::max(1, std::min(32, (team_budget(*ts) - xybuf) / per_prim));
+  c->bp = (T == 1) ? 1 : std::max(1, std::min(32, team_budget(T) / per_prim));
+  c->team_doubles = c->bp * per_prim;
+  c->team_doubles_f32 = c->bp * 4 + (c->bp * (18 + 3 * c->nroots * c->nI) + 1) / 2;
+
+  // ---- shared products path (FP64 launches of the classes where it measured faster):
+  // values ordered by their product; per pass the first product and the count.
+  // Lane programs share a product only within one lane's group and need no
+  // synchronisation; the shared path forms each product once per team in shared memory at
+  // the cost of a warp synchronisation and a shared-memory round trip per (primitive, root)
+  // step and a smaller batch.  Measured on GB300 the shared path wins for FP64 when a lane
+  // accumulates at least 20 values per pass, its products save at least a fifth of the
+  // multiplies, and the smaller batch costs no more root-phase lane iterations per primitive
+  // quartet (ceil(bp N / TS) / bp) than the larger one; for FP32 it never did.
+  if (T > 1) {
+    struct O { int comb, ie, jf; };
+    std::vector<O> ord;
+    for (int ie = 0; ie < c->ne; ++ie)
+      for (int jf = 0; jf < c->nf; ++jf) ord.push_back({eid[ie] * nfc + fid[jf], ie, jf});
+    std::stable_sort(ord.begin(), ord.end(), [](const O& x, const O& y) { return x.comb < y.comb; });
+    const int xnp = (c->nout + per_pass - 1) / per_pass;
+    std::vector<uint32_t> pinfo(2 * xnp);
+    int xymax = 0, xysum = 0;
+    for (int p = 0; p < xnp; ++p) {
+      const int o0 = p * per_pass, o1 = std::min(c->nout, o0 + per_pass) - 1;
+      pinfo[2 * p] = (uint32_t)ord[o0].comb;
+      pinfo[2 * p + 1] = (uint32_t)(ord[o1].comb - ord[o0].comb + 1);
+      xymax = std::max(xymax, (int)pinfo[2 * p + 1]);
+      xysum += (int)pinfo[2 * p + 1];
+    }
+    const int kcnt = std::min(32, (c->nout + T - 1) / T);
+    const int bp_on = std::max(1, std::min(32, (team_budget(T) - 2 * xymax) / per_prim));
+    auto iters = [&](int bp) { return (double)((bp * c->nroots + T - 1) / T) / bp; };
+    const bool fills = iters(bp_on) <= 1.1 * iters(c->bp);
+    c->xy = (kcnt >= 20 && 5 * xysum <= 4 * c->nout && fills) ? 1 : 0;
+    if (tune.xy >= 0) c->xy = tune.xy ? 1 : 0;
+    if (c->xy) {
+      c->xy_npass = xnp;
+      c->xymax = xymax;
+      c->xysum_xy = xysum;
+      c->bp_xy = bp_on;
+      c->team_doubles_xy = bp_on * per_prim + 2 * xymax;
+      std::vector<uint32_t> outi(c->nout), dst(c->nout);
+      for (int p = 0; p < xnp; ++p) {
+        const int o0 = p * per_pass, o1 = std::min(c->nout, o0 + per_pass) - 1;
+        for (int o = o0; o <= o1; ++o) {
+          const uint32_t iz = slot_word(ord[o].ie, ord[o].jf) & 0xff0000u;
+          outi[o] = (uint32_t)(ord[o].comb - (int)pinfo[2 * p]) | iz;
+          dst[o] = (uint32_t)(ord[o].ie * c->nf + ord[o].jf);
+        }
+      }
+      c->xy_outidx_off = (int)idx->size();
+      idx->insert(idx->end(), outi.begin(), outi.end());
+      c->xy_dst_off = (int)idx->size();
+      idx->insert(idx->end(), dst.begin(), dst.end());
+      c->xytab_off = (int)idx->size();
+      for (int a2 = 0; a2 < nec; ++a2)
+        for (int b2 = 0; b2 < nfc; ++b2) idx->push_back(slot_word(erep[a2] - c->e_base, frep[b2] - c->f_base) & 0xffffu);
+      c->pass_off = (int)idx->size();
+      idx->insert(idx->end(), pinfo.begin(), pinfo.end());
+    }
   }
-  c->team_doubles = c->bp * per_prim + xybuf;
-  c->team_doubles_f32 = c->bp * 4 + (c->bp * (18 + 3 * c->nroots * c->nI) + xybuf + 1) / 2;
   // HRR ping-pong size: max level size of the bra (vector nf) and ket (vector nab) passes
   long long m = 1;
   for (int k = 1; k <= lb; ++k) {
@@ -274,7 +337,6 @@ void make_class(int la, int lb, int lc, int ld, ClassDesc* c, int* ts, std::vect
   }
   c->hrr_doubles = (int)((m + 1) & ~1LL);
   c->scratch_per_team = ((long long)c->nout + 1) / 2 * 2 + 2LL * c->hrr_doubles;
-  c->outidx = nullptr;
 }
 
 // Fill the static part of a gradient class descriptor (Sec. 4): the four contracted sets,
@@ -374,11 +436,15 @@ eri_status device_init(int dev, DeviceState** out) {
     for (int X = 0; X < ERI_NPAIRTYPE; ++X)
       for (int Y = 0; Y < ERI_NPAIRTYPE; ++Y) {
         ClassDesc& cd = s.classes[X][Y];
-        cd.outidx = s.outidx + offs[X][Y];
+        const uint32_t* base = s.outidx + offs[X][Y];
+        cd.outidx = base;
+        cd.dst = base + cd.dst_off;
+        cd.gmask = base + cd.gmask_off;
         if (cd.xy) {
-          cd.xytab = cd.outidx + cd.xytab_off;
-          cd.dst = cd.outidx + cd.dst_off;
-          cd.passinfo = cd.outidx + cd.pass_off;
+          cd.xy_outidx = base + cd.xy_outidx_off;
+          cd.xy_dst = base + cd.xy_dst_off;
+          cd.xytab = base + cd.xytab_off;
+          cd.passinfo = base + cd.pass_off;
         }
       }
     all.clear();
@@ -426,9 +492,8 @@ void class_model_flops2(const ClassDesc& c, int nD, int want, int fp32, double* 
     vrr += Le * (3 * 3.0 + 3 * 5.0 * (Lf - 1));        // rows 1..Le
     mult += Le * (Lf - 1) + Le;
   }
-  // Eq. 1 products: a multiply and an FMA per value and root, or (products path) one
-  // multiply per shared product and an FMA per value
-  const double asm_ops = c.xy ? (double)c.xysum + 2.0 * c.nout : 3.0 * c.nout;
+  // Eq. 1 products: one multiply per shared I_x I_y product formed and an FMA per value
+  const double asm_ops = (double)((!fp32 && c.xy) ? c.xysum_xy : c.xysum) + 2.0 * c.nout;
   const double rec = N * (coef + mult + vrr) + N * asm_ops;
   double hrr = 0.0;
   for (int k = 1; k <= c.lb; ++k)
@@ -572,10 +637,11 @@ eri_status launch_shape(eri_plan* p, int X, int Y, int fp32, long long nteams_ne
   const ClassDesc& c = p->dev->classes[X][Y];
   const int ts = p->dev->ts[X][Y];
   const int teams_per_block = 128 / ts;
-  *smem = (int)(sizeof(double) * (size_t)(fp32 ? c.team_doubles_f32 : c.team_doubles) * teams_per_block);
+  *smem = (int)(sizeof(double) * (size_t)(fp32 ? c.team_doubles_f32 : (c.xy ? c.team_doubles_xy : c.team_doubles)) *
+                teams_per_block);
   if (*smem > 200 * 1024) return fail(ERI_ERR_ARG, "class (%d%d|%d%d) needs %d bytes of shared memory", c.la, c.lb, c.lc, c.ld, *smem);
   int bps = 0;
-  CUDA_TRY(erik_blocks_per_sm(ts, fp32, c.xy, *smem, &bps));
+  CUDA_TRY(erik_blocks_per_sm(ts, fp32, (c.xy && !fp32) ? 1 : 0, *smem, &bps));
   if (bps < 1) bps = 1;
   long long full = (long long)p->dev->sms * bps;
   long long need = (nteams_needed + teams_per_block - 1) / teams_per_block;
