@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--natm", type=int, default=30, help="atoms of the medium recipe (30 = the benchmark)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision measurement")
+    ap.add_argument("--no-grad", action="store_true", help="skip the gradient measurement")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target wall time of the oracle sample")
     return ap.parse_args()
 
@@ -260,9 +261,10 @@ def run_ours(args):
         for r in recs:
             prec = "float" if r["fp32"] else "double"
             if r["specialised"]:
-                key = f"eri_small_kernel<{r['la']}{r['lb']}{r['lc']}{r['ld']},{prec}>"
+                key = f"eri_small_kernel<{r['la']}, {r['lb']}, {r['lc']}, {r['ld']}, {prec}>"
             else:
-                key = f"eri_class_kernel<{r['team_size']},{prec}>"
+                xy = "true" if r["shared_products"] else "false"
+                key = f"eri_class_kernel<{r['team_size']}, {prec}, {xy}>"
             e = per_kernel.setdefault(key, {"ms": 0.0, "flops": 0.0, "launches": 0})
             e["ms"] += r["ms"]
             e["flops"] += r["model_flops"]
@@ -338,6 +340,36 @@ def run_ours(args):
                  "speedup_vs_fp64": (nsteps_total / tm) / value}
         plan_m.close()
 
+    # ---- J/K energy gradient (FP64) on the 12-atom cut of the same recipe, beside its J/K build
+    grad = None
+    if not args.no_grad:
+        mg = config_medium(seed=args.seed, natm=12)
+        plan_g = pkg.Plan(mg)
+        Dg = torch.from_numpy(np.ascontiguousarray(mg.D[0])).cuda()
+        gJ = torch.empty((mg.natm, 3), dtype=torch.float64, device="cuda")
+        gK = torch.empty_like(gJ)
+        plan_g.jk_grad(Dg, gJ, gK)
+        plan_g.jk(Dg)
+        torch.cuda.synchronize()
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        flush.zero_()
+        e0.record(stream)
+        plan_g.jk_grad(Dg, gJ, gK)
+        e1.record(stream)
+        flush.zero_()
+        e2.record(stream)
+        plan_g.jk(Dg)
+        e3 = torch.cuda.Event(enable_timing=True)
+        e3.record(stream)
+        torch.cuda.synchronize()
+        gst = plan_g.grad_stats()
+        tg, tj = e0.elapsed_time(e1) / 1e3, e2.elapsed_time(e3) / 1e3
+        grad = {"workload": "E_J / E_K nuclear gradient, medium recipe cut to 12 atoms (180 functions), FP64",
+                "value": 1.0 / tg, "unit": "gradients/s", "ms": 1e3 * tg, "jk_ms_same_molecule": 1e3 * tj,
+                "quartets_per_s": gst["quartets"] / tg, "prim_quartets_per_s": gst["prim_quartets"] / tg,
+                "max_abs_sum_over_atoms": float(max(gJ.sum(0).abs().max(), gK.sum(0).abs().max()))}
+        plan_g.close()
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         b, qs, cores, desc = oracle_sample_rate(mol, args.cpu_seconds)
@@ -370,6 +402,8 @@ def run_ours(args):
             "clocks": clocks,
             "cpu_baseline": cpu,
             "mixed": mixed,
+            "grad": grad,
+            "kernel_shares": {k: round(v["ms"] / all_ms, 4) for k, v in sorted(per_kernel.items(), key=lambda kv: -kv[1]["ms"])[:8]},
         }
         print(json.dumps(line), flush=True)
     dist.close()

@@ -196,6 +196,9 @@ typedef struct {
   double model_flops_fp32;        /* its FP32 part */
   int fp32;                       /* 1 for the FP32 path of ERI_MIXED */
   int specialised;                /* 1 for a compile-time specialised small-class kernel */
+  int shared_products;            /* 1 when the launch formed each I_x I_y product once per team in
+                                     shared memory; 0 for lane programs (products reused within a
+                                     lane) */
 } eri_launch_record;
 
 /* Turn per-launch CUDA-event timing of later eri_jk calls on (1) or off (0). */

@@ -1381,6 +1381,7 @@ eri_status eri_launch_records(eri_plan* p, eri_launch_record* out, int cap, int*
     r.model_flops_fp32 = a32 * (double)r.prim_quartets + q32 * (double)r.quartets;
     r.fp32 = f;
     r.specialised = p->last_launch_small[i];
+    r.shared_products = (!f && !r.specialised && c.xy) ? 1 : 0;
   }
   return ERI_OK;
 }
