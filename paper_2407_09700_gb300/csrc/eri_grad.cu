@@ -10,9 +10,10 @@
 //   1. primitive loop: Rys roots for L+1, 2D tables one order higher on the bra
 //      (Le+1) and on the ket (Lf+1), and four contracted sets of [e0|f0] (Eq. 1 products,
 //      Eq. 5 contraction): unweighted, and weighted per primitive quartet by 2 alpha,
-//      2 beta, 2 gamma (exponents of the primitives on centres A, B, C).  This is Eq. 10's
-//      linear map on the 2D integrals, d/dA_x = 2 alpha (+1_x) - a_x (-1_x), applied
-//      after contraction;
+//      2 beta, 2 gamma (exponents of the primitives on centres A, B, C), the weights folded
+//      into three scaled copies of the I_z table so that the sets share their I_x I_y
+//      products (lane programs).  This is Eq. 10's linear map on the 2D integrals,
+//      d/dA_x = 2 alpha (+1_x) - a_x (-1_x), applied after contraction;
 //   2. the six shifted blocks (a+-1 b|cd), (a b+-1|cd), (ab|c+-1 d) by the transfer
 //      relations, so d(ab|cd)/dA_x = (a+1_x b|cd)_{2 alpha} - a_x (a-1_x b|cd) and likewise
 //      for B and C; the derivative on D follows from translational invariance;
@@ -118,7 +119,8 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : 2)) eri_grad_kernel(const 
   const int N = g.nroots, nI = g.nI, Le2 = g.Le2, Lf2 = g.Lf2;
   const int bp = g.bp;
 
-  // team region: [bp][NPD] doubles, then [bp][GNPR], then [bp][3][N][nI]
+  // team region: [bp][NPD] doubles, then [bp][GNPR], then [bp][6][N][nI]: I_x, I_y and
+  // I_z scaled by 1, 2 alpha, 2 beta, 2 gamma
   Smem<double> sd, sr;
   if (TS == 1) {
     sd.base = smem + threadIdx.x;
@@ -178,10 +180,11 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : 2)) eri_grad_kernel(const 
 #pragma unroll
       for (int k = 0; k < GSLOTS; ++k) {
         const int o = o0 + k * TS + tl;
-        if (TS > 1) pkd[k] = (o < g.nout) ? __ldg(g.outidx + o) : 0u;
+        if (TS > 1) pkd[k] = (o < g.nslot) ? __ldg(g.outidx + o) : (1u << 31);
         acc[k] = 0.0;
       }
-      const int kcnt = min(GSLOTS, (g.nout - o0 + TS - 1) / TS);
+      const int kcnt = min(GSLOTS, (g.nslot - o0 + TS - 1) / TS);
+      const uint32_t gm = __ldg(g.gmask + pass);
 
       for (int q0 = 0; q0 < maxq; q0 += bp) {
         const int nbt = min(bp, nq - q0);
@@ -238,31 +241,36 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : 2)) eri_grad_kernel(const 
                                  fma(-u, sr[o + 8], sr[o + 2])};
             const double Cp[3] = {fma(u, sr[o + 9], sr[o + 3]), fma(u, sr[o + 10], sr[o + 4]),
                                   fma(u, sr[o + 11], sr[o + 5])};
-            const int g0 = S_2D + ((j * 3 + 0) * N + n) * nI;
+            const int g0 = S_2D + ((j * 6 + 0) * N + n) * nI;
             const int og[3] = {g0, g0 + N * nI, g0 + 2 * N * nI};
             rys_2d3<double>(sr, og, Le2, Lf2, wt, C, Cp, B00, B10, B01);
+            // the I_z table scaled by the primitive weights 2 alpha, 2 beta, 2 gamma
+            const double w1 = sr[o + 18], w2 = sr[o + 19], w3 = sr[o + 20];
+            for (int i = 0; i < nI; ++i) {
+              const double z = sr[og[2] + i];
+              sr[og[2] + N * nI + i] = w1 * z;
+              sr[og[2] + 2 * N * nI + i] = w2 * z;
+              sr[og[2] + 3 * N * nI + i] = w3 * z;
+            }
           }
         }
         __syncwarp();
-        // c. weighted assembly and contraction in registers
+        // c. assembly and contraction in registers by lane programs: a slot that starts a
+        //    group forms the group's I_x I_y product, each value adds product x weighted I_z
         for (int j = 0; j < bp; ++j) {
           if (j < nbt) {
-            const int o = j * GNPR;
-            const double w1 = sr[o + 18], w2 = sr[o + 19], w3 = sr[o + 20];
-            const int gx = S_2D + (j * 3 + 0) * N * nI;
-            const int gy = gx + N * nI;
-            const int gz = gy + N * nI;
+            for (int n = 0; n < N; ++n) {
+              const int gx = S_2D + ((j * 6 + 0) * N + n) * nI;
+              const int gy = gx + N * nI;
+              const int gz = gy + N * nI;
+              double v = 0.0;
 #pragma unroll
-            for (int k = 0; k < GSLOTS; ++k) {
-              if (k < kcnt) {
-                const uint32_t p = (TS == 1) ? __ldg(g.outidx + o0 + k) : pkd[k];
-                const int ox = (int)(p & 0xffu), oy = (int)((p >> 8) & 0xffu), oz = (int)((p >> 16) & 0xffu);
-                const int sel = (int)(p >> 24);
-                double t = 0.0;
-                for (int n = 0; n < N; ++n)
-                  t = fma(sr[gx + n * nI + ox] * sr[gy + n * nI + oy], sr[gz + n * nI + oz], t);
-                const double ws = (sel == 0) ? 1.0 : ((sel == 1) ? w1 : ((sel == 2) ? w2 : w3));
-                acc[k] = fma(ws, t, acc[k]);
+              for (int k = 0; k < GSLOTS; ++k) {
+                if (k < kcnt) {
+                  const uint32_t p = (TS == 1) ? __ldg(g.outidx + o0 + k) : pkd[k];
+                  if ((gm >> k) & 1u) v = sr[gx + (int)(p & 0xffu)] * sr[gy + (int)((p >> 8) & 0xffu)];
+                  acc[k] = fma(v, sr[gz + (int)((p >> 16) & 0xfffu)], acc[k]);
+                }
               }
             }
           }
@@ -273,7 +281,10 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : 2)) eri_grad_kernel(const 
 #pragma unroll
         for (int k = 0; k < GSLOTS; ++k) {
           const int o = o0 + k * TS + tl;
-          if (k < kcnt && o < g.nout) scr[o] = acc[k];
+          if (k < kcnt && o < g.nslot) {
+            const uint32_t p = (TS == 1) ? __ldg(g.outidx + o0 + k) : pkd[k];
+            if (!(p >> 31)) scr[__ldg(g.dst + o)] = acc[k];
+          }
         }
       }
     }

@@ -155,7 +155,10 @@ struct KernelArgs {
 //   set 1  weight 2 alpha e in [la+1, Le+1],      f in [lc, Lf]
 //   set 2  weight 2 beta  e in [la, Le+1],        f in [lc, Lf]
 //   set 3  weight 2 gamma e in [la, Le],          f in [lc+1, Lf+1]
-// (alpha, beta, gamma: exponents of the primitives on centres A, B, C).
+// (alpha, beta, gamma: exponents of the primitives on centres A, B, C).  Each primitive
+// quartet keeps four I_z tables scaled by the four weights, so every value of every set is
+// one FMA with a shared I_x I_y product (lane programs, as for the J/K classes): slot words
+// ix | iy << 8 | (k N nI + iz) << 16 | unused << 31, E0 positions dst, group starts gmask.
 struct GradDesc {
   int la, lb, lc, ld;
   int na, nb, nc, nd;
@@ -163,11 +166,15 @@ struct GradDesc {
   int s_elo[4], s_ne[4], s_flo[4], s_nf[4];   // first l and Cartesian count of e / f per set
   int s_off[4];                               // offset of each set in the team scratch
   int nout;                                   // total assembled values (sum of the four sets)
+  int nslot;                                  // lane-program slots (>= nout)
   int npass, bp, team_doubles;
   int gam_off;                                // Gamma_J, Gamma_K: 2 * na nb nc nd doubles
   int hrr_off, hrr_doubles;                   // two HRR ping-pong buffers
   long long scratch_per_team;
-  const uint32_t* outidx;                     // [nout] ix | iy << 8 | iz << 16 | set << 24
+  const uint32_t* outidx;                     // [nslot] slot words
+  const uint32_t* dst;                        // [nslot] position in the concatenated sets
+  const uint32_t* gmask;                      // [npass] group starts
+  int dst_off, gmask_off;                     // table offsets (host)
 };
 
 struct GradArgs {

@@ -142,6 +142,71 @@ ClassTune class_tune(int la, int lb, int lc, int ld) {
   return t;
 }
 
+// Lane programs: values with equal key (their I_x I_y product) form groups; groups are
+// split until every group size occurs a multiple of T times (a leftover group of size
+// s > 1 becomes s-1 and 1; a leftover of single values is padded) and dealt out so that
+// each lane of a T-lane team gets one group of each program entry.  Out: slot_val[o] =
+// value index or -1 (padding) for slot o = (k / 32) * 32 T + (k % 32) * T + lane of the
+// lane's k-th slot; gm[pass] bit k % 32 set where slot k starts a group (every pass starts
+// one); *slots_per_lane.
+void lane_programs(const std::vector<int>& key, int T, std::vector<int>* slot_val, std::vector<uint32_t>* gm,
+                   int* slots_per_lane) {
+  std::vector<std::pair<int, int>> kv;
+  for (int v = 0; v < (int)key.size(); ++v) kv.push_back({key[v], v});
+  std::stable_sort(kv.begin(), kv.end(), [](const std::pair<int, int>& x, const std::pair<int, int>& y) {
+    return x.first < y.first;
+  });
+  std::vector<std::vector<int>> groups;
+  for (size_t i = 0; i < kv.size(); ++i) {
+    if (i == 0 || kv[i].first != kv[i - 1].first) groups.emplace_back();
+    groups.back().push_back(kv[i].second);
+  }
+  int smax = 1;
+  for (const auto& g : groups) smax = std::max(smax, (int)g.size());
+  std::vector<std::vector<std::vector<int>>> bys(smax + 1);
+  for (auto& g : groups) bys[g.size()].push_back(g);
+  std::vector<std::vector<std::vector<int>>> lane(T);
+  std::vector<int> prog;
+  for (int sz = smax; sz >= 1; --sz) {
+    auto& L = bys[sz];
+    const int q = (int)L.size() / T, r = (int)L.size() % T;
+    for (int t = 0; t < q; ++t) {
+      prog.push_back(sz);
+      for (int ln = 0; ln < T; ++ln) lane[ln].push_back(L[t * T + ln]);
+    }
+    if (r) {
+      if (sz > 1) {
+        for (int t = q * T; t < (int)L.size(); ++t) {
+          std::vector<int> head(L[t].begin(), L[t].end() - 1), tail(1, L[t].back());
+          bys[sz - 1].push_back(head);
+          bys[1].push_back(tail);
+        }
+      } else {
+        prog.push_back(1);
+        for (int ln = 0; ln < T; ++ln) lane[ln].push_back(ln < r ? L[q * T + ln] : std::vector<int>(1, -1));
+      }
+    }
+  }
+  int Ls = 0;
+  for (int sz : prog) Ls += sz;
+  const int npass = (Ls + 31) / 32;
+  slot_val->assign((size_t)npass * 32 * T, -1);
+  slot_val->resize((size_t)Ls * T);
+  gm->assign(npass, 0u);
+  int k = 0;
+  for (int sz : prog) {
+    (*gm)[k / 32] |= 1u << (k % 32);
+    k += sz;
+  }
+  for (int p = 0; p < npass; ++p) (*gm)[p] |= 1u;
+  for (int ln = 0; ln < T; ++ln) {
+    int kk = 0;
+    for (const auto& g : lane[ln])
+      for (size_t m = 0; m < g.size(); ++m, ++kk) (*slot_val)[(kk / 32) * 32 * T + (kk % 32) * T + ln] = g[m];
+  }
+  *slots_per_lane = Ls;
+}
+
 // Fill the static part of a class descriptor (no device pointers).  idx receives the
 // class's u32 tables: lane-program outidx [nslot], dst [nslot], gmask [npass], then (xy
 // classes) the shared-products tables xy_outidx [nout], xy_dst [nout], xytab [ncomb],
@@ -194,66 +259,25 @@ void make_class(int la, int lb, int lc, int ld, ClassDesc* c, int* ts, std::vect
            ((uint32_t)(ct.lz[e] * L1 + ct.lz[f]) << 16);
   };
 
-  // ---- lane programs: groups of values sharing a product, split until every group size
-  // occurs a multiple of TS times (a leftover group of size s > 1 becomes s-1 and 1; a
-  // leftover of single values is padded), then dealt out so each lane gets one group of
-  // each program entry
+  // ---- lane programs (products reused within a lane's group)
   {
-    std::vector<std::vector<int>> groups(c->ncomb);
+    std::vector<int> key(c->nout);
     for (int ie = 0; ie < c->ne; ++ie)
-      for (int jf = 0; jf < c->nf; ++jf) groups[eid[ie] * nfc + fid[jf]].push_back(ie * c->nf + jf);
-    int smax = 1;
-    for (const auto& g : groups) smax = std::max(smax, (int)g.size());
-    std::vector<std::vector<std::vector<int>>> bys(smax + 1);
-    for (auto& g : groups)
-      if (!g.empty()) bys[g.size()].push_back(g);
-    std::vector<std::vector<std::vector<int>>> lane(T);
-    std::vector<int> prog;
-    for (int sz = smax; sz >= 1; --sz) {
-      auto& L = bys[sz];
-      const int q = (int)L.size() / T, r = (int)L.size() % T;
-      for (int t = 0; t < q; ++t) {
-        prog.push_back(sz);
-        for (int ln = 0; ln < T; ++ln) lane[ln].push_back(L[t * T + ln]);
-      }
-      if (r) {
-        if (sz > 1) {
-          for (int t = q * T; t < (int)L.size(); ++t) {
-            std::vector<int> head(L[t].begin(), L[t].end() - 1), tail(1, L[t].back());
-            bys[sz - 1].push_back(head);
-            bys[1].push_back(tail);
-          }
-        } else {
-          prog.push_back(1);
-          for (int ln = 0; ln < T; ++ln) lane[ln].push_back(ln < r ? L[q * T + ln] : std::vector<int>(1, -1));
-        }
-      }
-    }
+      for (int jf = 0; jf < c->nf; ++jf) key[ie * c->nf + jf] = eid[ie] * nfc + fid[jf];
+    std::vector<int> sv;
+    std::vector<uint32_t> gm;
     int Ls = 0;
-    for (int sz : prog) Ls += sz;
+    lane_programs(key, T, &sv, &gm, &Ls);
     c->nslot = Ls * T;
-    c->npass = (Ls + 31) / 32;
-    std::vector<uint32_t> outi(c->nslot, 1u << 31), dst(c->nslot, 0), gm(c->npass, 0);
-    std::vector<int> start(Ls, 0);
-    int k = 0;
-    for (int sz : prog) {
-      for (int m = 0; m < sz; ++m) start[k + m] = (m == 0);
-      k += sz;
-    }
-    for (int k2 = 0; k2 < Ls; k2 += 32) start[k2] = 1;        // a pass starts with a product
-    for (int k2 = 0; k2 < Ls; ++k2)
-      if (start[k2]) gm[k2 / 32] |= 1u << (k2 % 32);
+    c->npass = (int)gm.size();
+    std::vector<uint32_t> outi(c->nslot, 1u << 31), dst(c->nslot, 0);
     int xys = 0;
-    for (int ln = 0; ln < T; ++ln) {
-      int kk = 0;
-      for (const auto& g : lane[ln])
-        for (size_t m = 0; m < g.size(); ++m, ++kk) {
-          const int o = (kk / 32) * per_pass + (kk % 32) * T + ln;
-          if (g[m] < 0) continue;
-          outi[o] = slot_word(g[m] / c->nf, g[m] % c->nf);
-          dst[o] = (uint32_t)g[m];
-          if (start[kk]) ++xys;
-        }
+    for (int o = 0; o < c->nslot; ++o) {
+      if (sv[o] < 0) continue;
+      outi[o] = slot_word(sv[o] / c->nf, sv[o] % c->nf);
+      dst[o] = (uint32_t)sv[o];
+      const int k = (o / (32 * T)) * 32 + (o % (32 * T)) / T;
+      if ((gm[k / 32] >> (k % 32)) & 1u) ++xys;
     }
     c->xysum = xys;
     idx->insert(idx->end(), outi.begin(), outi.end());
@@ -354,7 +378,12 @@ void make_grad_class(int la, int lb, int lc, int ld, GradDesc* g, int* ts, std::
   const int flo[4] = {std::max(lc - 1, 0), lc, lc, lc + 1}, fhi[4] = {Lf, Lf, Lf, Lf + 1};
   const CartTab& ct = cart();
   const int L1 = g->Lf2 + 1;
+  const int NnI = g->nroots * g->nI;
   idx->clear();
+  // values of the four sets (set k, e, f) at S position s_off[k] + ie * s_nf[k] + jf; their
+  // I_x I_y key and their I_z offset within the four weighted z tables of a primitive quartet
+  std::vector<int> key;
+  std::vector<uint32_t> word;
   int off = 0;
   for (int k = 0; k < 4; ++k) {
     g->s_elo[k] = elo[k];
@@ -367,15 +396,32 @@ void make_grad_class(int la, int lb, int lc, int ld, GradDesc* g, int* ts, std::
         const int e = cart_below(elo[k]) + ie, f = cart_below(flo[k]) + jf;
         const uint32_t ix = ct.lx[e] * L1 + ct.lx[f];
         const uint32_t iy = ct.ly[e] * L1 + ct.ly[f];
-        const uint32_t iz = ct.lz[e] * L1 + ct.lz[f];
-        idx->push_back(ix | (iy << 8) | (iz << 16) | ((uint32_t)k << 24));
+        const uint32_t iz = (uint32_t)(k * NnI) + ct.lz[e] * L1 + ct.lz[f];
+        key.push_back((int)(ix | (iy << 8)));
+        word.push_back(ix | (iy << 8) | (iz << 16));
       }
     off += g->s_ne[k] * g->s_nf[k];
   }
   g->nout = off;
   *ts = choose_ts(g->nout);
-  g->npass = (g->nout + *ts * 32 - 1) / (*ts * 32);
-  const int per_prim = 4 + 21 + 3 * g->nroots * g->nI;
+  std::vector<int> sv;
+  std::vector<uint32_t> gm;
+  int Ls = 0;
+  lane_programs(key, *ts, &sv, &gm, &Ls);
+  g->nslot = Ls * *ts;
+  g->npass = (int)gm.size();
+  std::vector<uint32_t> dst(g->nslot, 0);
+  for (int o = 0; o < g->nslot; ++o) {
+    idx->push_back(sv[o] < 0 ? (1u << 31) : word[sv[o]]);
+    if (sv[o] >= 0) dst[o] = (uint32_t)sv[o];
+  }
+  g->dst_off = (int)idx->size();
+  idx->insert(idx->end(), dst.begin(), dst.end());
+  g->gmask_off = (int)idx->size();
+  idx->insert(idx->end(), gm.begin(), gm.end());
+  // per primitive quartet: 4 doubles (table lookup) + 21 scalars + the I_x, I_y tables and
+  // four weighted I_z tables (weights 1, 2 alpha, 2 beta, 2 gamma)
+  const int per_prim = 4 + 21 + 6 * NnI;
   if (*ts == 1) {
     g->bp = 1;
   } else {
@@ -460,7 +506,12 @@ eri_status device_init(int dev, DeviceState** out) {
     CUDA_TRY(cudaMalloc(&s.grad_outidx, sizeof(uint32_t) * all.size()));
     CUDA_TRY(cudaMemcpy(s.grad_outidx, all.data(), sizeof(uint32_t) * all.size(), cudaMemcpyHostToDevice));
     for (int X = 0; X < ERI_NPAIRTYPE; ++X)
-      for (int Y = 0; Y < ERI_NPAIRTYPE; ++Y) s.gclasses[X][Y].outidx = s.grad_outidx + offs[X][Y];
+      for (int Y = 0; Y < ERI_NPAIRTYPE; ++Y) {
+        GradDesc& gd = s.gclasses[X][Y];
+        gd.outidx = s.grad_outidx + offs[X][Y];
+        gd.dst = gd.outidx + gd.dst_off;
+        gd.gmask = gd.outidx + gd.gmask_off;
+      }
     CUDA_TRY(cudaDeviceGetAttribute(&s.sms, cudaDevAttrMultiProcessorCount, dev));
     s.ready = true;
   }
