@@ -291,6 +291,12 @@ void make_class(int la, int lb, int lc, int ld, ClassDesc* c, int* ts, std::vect
   c->bp = (T == 1) ? 1 : std::max(1, std::min(32, team_budget(T) / per_prim));
   c->team_doubles = c->bp * per_prim;
   c->team_doubles_f32 = c->bp * 4 + (c->bp * (18 + 3 * c->nroots * c->nI) + 1) / 2;
+  // Team regions of a block start an odd number of doubles apart, so the teams of a warp
+  // reading the same table entry hit distinct shared-memory banks.
+  if (T > 1) {
+    c->team_doubles |= 1;
+    c->team_doubles_f32 |= 1;
+  }
 
   // ---- shared products path (FP64 launches of the classes where it measured faster):
   // values ordered by their product; per pass the first product and the count.
@@ -328,7 +334,7 @@ void make_class(int la, int lb, int lc, int ld, ClassDesc* c, int* ts, std::vect
       c->xymax = xymax;
       c->xysum_xy = xysum;
       c->bp_xy = bp_on;
-      c->team_doubles_xy = bp_on * per_prim + 2 * xymax;
+      c->team_doubles_xy = (bp_on * per_prim + 2 * xymax) | 1;
       std::vector<uint32_t> outi(c->nout), dst(c->nout);
       for (int p = 0; p < xnp; ++p) {
         const int o0 = p * per_pass, o1 = std::min(c->nout, o0 + per_pass) - 1;
@@ -428,6 +434,7 @@ void make_grad_class(int la, int lb, int lc, int ld, GradDesc* g, int* ts, std::
     g->bp = std::max(1, std::min(32, team_budget(*ts) / per_prim));
   }
   g->team_doubles = g->bp * per_prim;
+  if (*ts > 1) g->team_doubles |= 1;      // odd team stride: distinct banks across teams
   const int nabcd = g->na * g->nb * g->nc * g->nd;
   g->gam_off = (off + 1) & ~1;
   g->hrr_off = g->gam_off + ((2 * nabcd + 1) & ~1);
