@@ -241,6 +241,15 @@ eri_status eri_batch_stats(eri_batch* batch, long long* quartets, long long* qua
 eri_status eri_one_electron(const eri_basis* basis, int ncharge, const double* charge_xyz,
                             const double* charges, double* S, double* T, double* V);
 
+/*
+ * Host self-check of the per-class assembly tables, needs no GPU: for every J/K class and
+ * every gradient class, each [e0|f0] value is assembled by exactly one slot, each slot's
+ * 2D-table offsets belong to its value, slots that reuse an I_x I_y product share it with
+ * the slot that formed it, and the team regions fit in shared memory.  Writes the number
+ * of classes checked and of violations found (0 expected).  Honours ERI_CLASS_CONFIG.
+ */
+eri_status eri_check_class_tables(int* nclasses, int* problems);
+
 /* Counters of the last eri_jk call (synchronises that call's stream). */
 eri_status eri_flop_stats(eri_plan* plan, eri_stats* out);
 

@@ -11,7 +11,11 @@
 #define TPB 128        // threads per block of the class kernels
 #define GSLOTS 32      // accumulator slots per lane
 
-static __constant__ unsigned char c_cart[ERI_MAXCART][4];   // lx, ly, lz, l by global Cartesian index
+// lx, ly, lz, l by global Cartesian index.  Global memory read through the read-only
+// path (L1-resident, 880 bytes): lanes of a team read different entries, which constant
+// memory would serialise.
+static __device__ uchar4 c_cart[ERI_MAXCART];
+__device__ __forceinline__ uchar4 cart_of(int g) { return __ldg(c_cart + g); }
 
 __device__ __forceinline__ int cart_below(int l) { return l * (l + 1) * (l + 2) / 6; }
 __device__ __forceinline__ int cart_pos(int ly, int lz) { int r = ly + lz; return r * (r + 1) / 2 + lz; }
@@ -155,13 +159,13 @@ __device__ const R* hrr_team(int la, int lb, const double* AB, int nv, const R* 
         const int r = t / nv;
         const int ib = r % nb;
         const int ia = r / nb;
-        const unsigned char* av = c_cart[base + ia];
-        const unsigned char* bv = c_cart[cart_below(k) + ib];
-        const int i = bv[0] ? 0 : (bv[1] ? 1 : 2);
-        int bm[3] = {bv[0], bv[1], bv[2]};
+        const uchar4 av = cart_of(base + ia);
+        const uchar4 bv = cart_of(cart_below(k) + ib);
+        const int i = bv.x ? 0 : (bv.y ? 1 : 2);
+        int bm[3] = {bv.x, bv.y, bv.z};
         bm[i] -= 1;
         const int ibm = cart_pos(bm[1], bm[2]);
-        int ap[3] = {av[0], av[1], av[2]};
+        int ap[3] = {av.x, av.y, av.z};
         ap[i] += 1;
         const int iap = cart_index(ap[0], ap[1], ap[2]) - base;
         const R hi = cur[iap * cse + ibm * csb + v * csv];

@@ -57,10 +57,10 @@ __device__ __forceinline__ void contract_shift(const double* G, int sab, int scd
     const int i0 = r / m[1];
     const double v = G[(i0 * m[1] + i1) * sab + (i2 * m[3] + i3) * scd];
     const int is = (pos == 0) ? i0 : (pos == 1 ? i1 : i2);
-    const unsigned char* cv = c_cart[base + is];
+    const uchar4 cv = cart_of(base + is);
 #pragma unroll
     for (int x = 0; x < 3; ++x) {
-      int q[3] = {cv[0], cv[1], cv[2]};
+      int q[3] = {cv.x, cv.y, cv.z};
       double coef;
       if (plus) {
         if (q[x] == 0) continue;
@@ -400,15 +400,12 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : 2)) eri_grad_kernel(const 
 
 // ------------------------------------------------------------------ host launchers
 extern "C" int erik_upload_cart_tables_grad(void) {
-  unsigned char h[ERI_MAXCART][4];
+  uchar4 h[ERI_MAXCART];
   int g = 0;
   for (int l = 0; l <= ERI_CART_LMAX; ++l)
     for (int lx = l; lx >= 0; --lx)
       for (int ly = l - lx; ly >= 0; --ly) {
-        h[g][0] = (unsigned char)lx;
-        h[g][1] = (unsigned char)ly;
-        h[g][2] = (unsigned char)(l - lx - ly);
-        h[g][3] = (unsigned char)l;
+        h[g] = make_uchar4((unsigned char)lx, (unsigned char)ly, (unsigned char)(l - lx - ly), (unsigned char)l);
         ++g;
       }
   return (int)cudaMemcpyToSymbol(c_cart, h, sizeof(h));

@@ -520,15 +520,12 @@ __global__ void fma_probe_kernel(Tp* out, int iters, Tp a, Tp b) {
 
 // ------------------------------------------------------------------ host launchers
 extern "C" int erik_upload_cart_tables(void) {
-  unsigned char h[ERI_MAXCART][4];
+  uchar4 h[ERI_MAXCART];
   int g = 0;
   for (int l = 0; l <= ERI_CART_LMAX; ++l)
     for (int lx = l; lx >= 0; --lx)
       for (int ly = l - lx; ly >= 0; --ly) {
-        h[g][0] = (unsigned char)lx;
-        h[g][1] = (unsigned char)ly;
-        h[g][2] = (unsigned char)(l - lx - ly);
-        h[g][3] = (unsigned char)l;
+        h[g] = make_uchar4((unsigned char)lx, (unsigned char)ly, (unsigned char)(l - lx - ly), (unsigned char)l);
         ++g;
       }
   return (int)cudaMemcpyToSymbol(c_cart, h, sizeof(h));

@@ -1444,6 +1444,100 @@ eri_status eri_launch_records(eri_plan* p, eri_launch_record* out, int cap, int*
   return ERI_OK;
 }
 
+// Host self-check of the per-class tables (no GPU needed): every [e0|f0] value of every
+// J/K and gradient class appears exactly once among the slots, each slot's 2D-table
+// offsets belong to its value, a slot that does not start a group shares its group's
+// I_x I_y offsets, every pass starts a group, offsets stay inside the tables and the team
+// regions fit in shared memory.
+eri_status eri_check_class_tables(int* nclasses, int* problems) {
+  g_err.clear();
+  if (!nclasses || !problems) return fail(ERI_ERR_ARG, "NULL output");
+  const CartTab& ct = cart();
+  int bad = 0, n = 0;
+  auto check_lp = [&](const uint32_t* outi, const uint32_t* dst, const uint32_t* gm, int T, int nslot, int nval,
+                      auto&& expect) {
+    const int Ls = nslot / T;
+    if (Ls * T != nslot) ++bad;
+    std::vector<int> seen(nval, 0);
+    for (int p = 0; p < (Ls + 31) / 32; ++p)
+      if (!(gm[p] & 1u)) ++bad;
+    for (int ln = 0; ln < T; ++ln) {
+      uint32_t cur = 0xffffffffu;
+      for (int k = 0; k < Ls; ++k) {
+        const int o = (k / 32) * T * 32 + (k % 32) * T + ln;
+        const uint32_t q = outi[o];
+        if ((gm[k / 32] >> (k % 32)) & 1u) cur = q & 0xffffu;
+        if (q >> 31) continue;
+        if ((q & 0xffffu) != cur) ++bad;
+        if ((int)dst[o] < 0 || (int)dst[o] >= nval) { ++bad; continue; }
+        if (seen[dst[o]]++) ++bad;
+        if (!expect((int)dst[o], q)) ++bad;
+      }
+    }
+    for (int v = 0; v < nval; ++v)
+      if (seen[v] != 1) ++bad;
+  };
+  for (int X = 0; X < ERI_NPAIRTYPE; ++X)
+    for (int Y = 0; Y < ERI_NPAIRTYPE; ++Y) {
+      int la, lb, lc, ld, ts;
+      ptype_ls(X, &la, &lb);
+      ptype_ls(Y, &lc, &ld);
+      {
+        ClassDesc c;
+        std::vector<uint32_t> idx;
+        make_class(la, lb, lc, ld, &c, &ts, &idx);
+        ++n;
+        const int L1 = c.Lf + 1;
+        auto word = [&](int v) {
+          const int e = c.e_base + v / c.nf, f = c.f_base + v % c.nf;
+          return (uint32_t)(ct.lx[e] * L1 + ct.lx[f]) | ((uint32_t)(ct.ly[e] * L1 + ct.ly[f]) << 8) |
+                 ((uint32_t)(ct.lz[e] * L1 + ct.lz[f]) << 16);
+        };
+        check_lp(idx.data(), idx.data() + c.dst_off, idx.data() + c.gmask_off, ts, c.nslot, c.nout,
+                 [&](int v, uint32_t q) { return (q & 0xffffffu) == word(v); });
+        const int tpb = 128 / ts;
+        if (ts > 1 && (8L * c.team_doubles * tpb > 200 * 1024 || 8L * c.team_doubles_f32 * tpb > 200 * 1024)) ++bad;
+        if (c.xy) {
+          if (8L * c.team_doubles_xy * tpb > 200 * 1024) ++bad;
+          const uint32_t* xo = idx.data() + c.xy_outidx_off;
+          const uint32_t* xd = idx.data() + c.xy_dst_off;
+          const uint32_t* xt = idx.data() + c.xytab_off;
+          const uint32_t* pi = idx.data() + c.pass_off;
+          std::vector<int> seen(c.nout, 0);
+          for (int o = 0; o < c.nout; ++o) {
+            const int p = o / (32 * ts);
+            const uint32_t q = xo[o] & 0xffffu;
+            if (q >= pi[2 * p + 1] || (int)pi[2 * p + 1] > c.xymax) { ++bad; continue; }
+            const uint32_t w = word((int)xd[o]);
+            if (((xt[pi[2 * p] + q]) & 0xffffu) != (w & 0xffffu) || (xo[o] & 0xff0000u) != (w & 0xff0000u)) ++bad;
+            if (seen[xd[o]]++) ++bad;
+          }
+        }
+      }
+      {
+        GradDesc g;
+        std::vector<uint32_t> idx;
+        make_grad_class(la, lb, lc, ld, &g, &ts, &idx);
+        ++n;
+        const int L1 = g.Lf2 + 1, NnI = g.nroots * g.nI;
+        auto expect = [&](int v, uint32_t q) {
+          int set = 0;
+          while (set < 3 && v >= g.s_off[set + 1]) ++set;
+          const int r = v - g.s_off[set], ie = r / g.s_nf[set], jf = r % g.s_nf[set];
+          const int e = cart_below(g.s_elo[set]) + ie, f = cart_below(g.s_flo[set]) + jf;
+          return (q & 0xffu) == (uint32_t)(ct.lx[e] * L1 + ct.lx[f]) &&
+                 ((q >> 8) & 0xffu) == (uint32_t)(ct.ly[e] * L1 + ct.ly[f]) &&
+                 ((q >> 16) & 0xfffu) == (uint32_t)(set * NnI + ct.lz[e] * L1 + ct.lz[f]);
+        };
+        check_lp(idx.data(), idx.data() + g.dst_off, idx.data() + g.gmask_off, ts, g.nslot, g.nout, expect);
+        if (ts > 1 && 8L * g.team_doubles * (128 / ts) > 200 * 1024) ++bad;
+      }
+    }
+  *nclasses = n;
+  *problems = bad;
+  return ERI_OK;
+}
+
 eri_status eri_probe_fma_peak(double* fp64_tflops, double* fp32_tflops) {
   g_err.clear();
   if (!fp64_tflops || !fp32_tflops) return fail(ERI_ERR_ARG, "NULL output");

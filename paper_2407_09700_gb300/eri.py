@@ -91,6 +91,7 @@ _SIGS = {
                                     ctypes.POINTER(ctypes.c_int), ctypes.c_void_p]),
     "eri_batch_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong),
                                        ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_int)]),
+    "eri_check_class_tables": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "eri_last_error": (ctypes.c_char_p, []),
 }
 
@@ -268,6 +269,13 @@ def rys_roots(N, T):
     w = np.zeros((T.size, N))
     _check(load_library().eri_rys_roots(int(N), int(T.size), _d(T), _d(u), _d(w)))
     return u, w
+
+
+def check_class_tables():
+    """(classes checked, violations) of the host self-check of the per-class tables."""
+    n, bad = ctypes.c_int(), ctypes.c_int()
+    _check(load_library().eri_check_class_tables(ctypes.byref(n), ctypes.byref(bad)))
+    return n.value, bad.value
 
 
 def probe_fma_peak():

@@ -77,3 +77,28 @@ def test_rys_and_jk_argument_checks(lib):
     assert lib.eri_jk(None, None, 1, None, None, 3, None) == E.ERI_ERR_ARG
     assert lib.eri_plan_nbf(None) == -1
     assert lib.eri_plan_destroy(None) == E.ERI_OK
+
+
+def test_class_tables_self_check(lib):
+    """Every J/K and gradient class's slot tables cover each value once with its own 2D
+    offsets, shared products stay within a group, and the team regions fit (host only)."""
+    n, bad = pkg.check_class_tables()
+    assert n == 2 * 15 * 15
+    assert bad == 0
+
+
+def test_class_tables_self_check_with_overrides(lib):
+    """The tuning override (team sizes 2/4/8/32, shared products forced on or off) keeps the
+    tables consistent; the override is read once per process, so run it in a child."""
+    import os
+    import subprocess
+    import sys
+    cfg = "1 1 1 1 2 0;2 1 2 1 4 1;2 2 2 2 8 1;2 0 1 0 4 0;4 4 4 4 32 0;3 2 1 1 2 -1;2 2 1 0 32 1"
+    env = dict(os.environ, ERI_CLASS_CONFIG=cfg)
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = "import paper_2407_09700_gb300 as p; print(*p.check_class_tables())"
+    out = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True, text=True,
+                         timeout=300)
+    assert out.returncode == 0, out.stderr
+    n, bad = map(int, out.stdout.split())
+    assert n == 450 and bad == 0

@@ -240,3 +240,68 @@ def test_batch_same_alone_and_in_the_mix():
     st = batch.stats()
     total = sum(p.stats()["quartets_computed"] for p in plans)
     assert st["quartets"] == total
+
+
+_OVERRIDE_CHILD = r"""
+import sys, json
+import numpy as np, torch
+sys.path.insert(0, ".")
+import paper_2407_09700_gb300 as pkg
+from workloads import custom_molecule, random_psd_density
+rng = np.random.default_rng(11)
+coords = rng.uniform(-1.6, 1.6, (3, 3))
+shells = []
+for a in range(3):
+    for l in range(3):
+        K = int(rng.integers(1, 4))
+        shells.append((a, l, np.sort(rng.uniform(0.2, 3.0, K))[::-1], rng.uniform(0.2, 1.0, K)))
+m = custom_molecule(coords, shells)
+D = random_psd_density(m.nbf, 6, rng)
+np.save(sys.argv[1], D)
+out = {}
+for name, prec in (("fp64", pkg.ERI_FP64), ("mixed", pkg.ERI_MIXED)):
+    plan = pkg.Plan(m, tau=0.0, precision=prec, mixed_thresh=1e-2)
+    J, K = plan.jk(torch.from_numpy(D).cuda())
+    torch.cuda.synchronize()
+    out[name] = [J.cpu().numpy().tolist(), K.cpu().numpy().tolist()]
+    plan.close()
+print(json.dumps(out))
+"""
+
+
+@pytest.mark.parametrize("cfg", [
+    # every s/p/d team class forced to 2 or 4 lanes, shared products on where allowed
+    "1 1 1 1 2 1;2 0 1 1 2 1;2 0 2 0 4 1;2 1 1 0 4 1;2 1 1 1 2 1;2 1 2 0 4 1;2 1 2 1 2 1;2 2 1 0 2 1;"
+    "2 2 1 1 4 1;2 2 2 0 2 1;2 2 2 1 4 1;2 2 2 2 8 1",
+    # the same classes at 8 and 32 lanes with lane programs only
+    "1 1 1 1 32 0;2 0 1 1 8 0;2 0 2 0 32 0;2 1 1 0 8 0;2 1 1 1 32 0;2 1 2 0 8 0;2 1 2 1 32 0;2 2 1 0 8 0;"
+    "2 2 1 1 8 0;2 2 2 0 32 0;2 2 2 1 32 0;2 2 2 2 32 0",
+])
+def test_jk_team_size_overrides(tmp_path, cfg):
+    """The tuning override changes team sizes and the assembly path, never the result:
+    J and K against the oracle at 1e-10 (FP64) and 1e-6 (mixed), in a child process (the
+    override is read once per process)."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    dpath = str(tmp_path / "D.npy")
+    res = subprocess.run([sys.executable, "-c", _OVERRIDE_CHILD, dpath], cwd=root, capture_output=True, text=True,
+                         env=dict(os.environ, ERI_CLASS_CONFIG=cfg), timeout=600)
+    assert res.returncode == 0, res.stderr[-2000:]
+    out = json.loads(res.stdout.strip().splitlines()[-1])
+    rng = np.random.default_rng(11)
+    coords = rng.uniform(-1.6, 1.6, (3, 3))
+    shells = []
+    for a in range(3):
+        for l in range(3):
+            K = int(rng.integers(1, 4))
+            shells.append((a, l, np.sort(rng.uniform(0.2, 3.0, K))[::-1], rng.uniform(0.2, 1.0, K)))
+    m = custom_molecule(coords, shells)
+    D = np.load(dpath)
+    Jr, Kr, _ = oracle.jk(m, D=D, screen=False)
+    for name, tol in (("fp64", 1e-10), ("mixed", 1e-6)):
+        J, K = (np.array(x).reshape(Jr.shape) for x in out[name])
+        assert np.abs(J - Jr).max() <= tol, (name, np.abs(J - Jr).max())
+        assert np.abs(K - Kr).max() <= tol, (name, np.abs(K - Kr).max())
