@@ -137,6 +137,40 @@ __device__ __forceinline__ void rys_2d3(const Smem<R>& g, const int o[3], int Le
   }
 }
 
+// The same recurrences for one axis: I(n, m) at g[o + n*(Lf+1) + m] from I(0,0) = I00
+// (1 for x and y, w Theta for z).  Used when the (primitive, root) items of a batch are
+// too few to fill a team, so the three axes run on separate lanes.
+template <typename R>
+__device__ __forceinline__ void rys_2d1(const Smem<R>& g, int o, int Le, int Lf, R I00, R C, R Cp, R B00, R B10,
+                                        R B01) {
+  const int L1 = Lf + 1;
+  g[o] = I00;
+  if (Le >= 1) g[o + L1] = C * I00;
+  R nb10 = B10;
+  for (int n = 1; n < Le; ++n) {
+    g[o + (n + 1) * L1] = fma(C, g[o + n * L1], nb10 * g[o + (n - 1) * L1]);
+    nb10 += B10;
+  }
+  if (Lf == 0) return;
+  g[o + 1] = Cp * I00;
+  R mb01 = B01;
+  for (int m = 1; m < Lf; ++m) {
+    g[o + m + 1] = fma(Cp, g[o + m], mb01 * g[o + m - 1]);
+    mb01 += B01;
+  }
+  R nb00 = B00;
+  for (int n = 1; n <= Le; ++n) {
+    const int r = o + n * L1;
+    g[r + 1] = fma(Cp, g[r], nb00 * g[r - L1]);
+    R mb = B01;
+    for (int m = 1; m < Lf; ++m) {
+      g[r + m + 1] = fma(Cp, g[r + m], fma(nb00, g[r + m - L1], mb * g[r + m - 1]));
+      mb += B01;
+    }
+    nb00 += B00;
+  }
+}
+
 // ------------------------------------------------------------------ transfer (horizontal) relations
 // Input element (e, v) at X[e*xe + v*xv] for la <= |e| <= la+lb (e relative to cart_below(la)).
 // Output contiguous [a][b][v] with |a| = la, |b| = lb; returns the output pointer (X when lb = 0).

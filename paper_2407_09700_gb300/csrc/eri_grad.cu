@@ -225,32 +225,63 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : 2)) eri_grad_kernel(const 
           }
         }
         __syncwarp();
-        // b. roots, weights and the 2D tables per (primitive, root)
-        for (int tk = tl; tk < bp * N; tk += TS) {
-          const int j = tk / N, n = tk - (tk / N) * N;
-          if (j < nbt) {
-            const int od = j * NPD, o = j * GNPR;
-            double u, w;
-            rys_root(a.rys_coef, a.rys_au, a.rys_aw, N, (int)__double_as_longlong(sd[od + 3]), sd[od + 0],
-                     sd[od + 1], sd[od + 2], n, u, w);
-            const double B00 = u * sr[o + 12];
-            const double B10 = fma(-u, sr[o + 13], sr[o + 16]);
-            const double B01 = fma(-u, sr[o + 14], sr[o + 17]);
-            const double wt = w * sr[o + 15];
-            const double C[3] = {fma(-u, sr[o + 6], sr[o + 0]), fma(-u, sr[o + 7], sr[o + 1]),
-                                 fma(-u, sr[o + 8], sr[o + 2])};
-            const double Cp[3] = {fma(u, sr[o + 9], sr[o + 3]), fma(u, sr[o + 10], sr[o + 4]),
-                                  fma(u, sr[o + 11], sr[o + 5])};
-            const int g0 = S_2D + ((j * 6 + 0) * N + n) * nI;
-            const int og[3] = {g0, g0 + N * nI, g0 + 2 * N * nI};
-            rys_2d3<double>(sr, og, Le2, Lf2, wt, C, Cp, B00, B10, B01);
-            // the I_z table scaled by the primitive weights 2 alpha, 2 beta, 2 gamma
-            const double w1 = sr[o + 18], w2 = sr[o + 19], w3 = sr[o + 20];
-            for (int i = 0; i < nI; ++i) {
-              const double z = sr[og[2] + i];
-              sr[og[2] + N * nI + i] = w1 * z;
-              sr[og[2] + 2 * N * nI + i] = w2 * z;
-              sr[og[2] + 3 * N * nI + i] = w3 * z;
+        // b. roots, weights and the 2D tables per (primitive, root), or per (primitive, root,
+        //    axis) when that fills more of the team's lanes
+        if (TS > 1 && g.split3) {
+          for (int tk = tl; tk < bp * N * 3; tk += TS) {
+            const int jn = tk / 3, ax = tk - jn * 3;
+            const int j = jn / N, n = jn - (jn / N) * N;
+            if (j < nbt) {
+              const int od = j * NPD, o = j * GNPR;
+              double u, w;
+              rys_root(a.rys_coef, a.rys_au, a.rys_aw, N, (int)__double_as_longlong(sd[od + 3]), sd[od + 0],
+                       sd[od + 1], sd[od + 2], n, u, w);
+              const double B00 = u * sr[o + 12];
+              const double B10 = fma(-u, sr[o + 13], sr[o + 16]);
+              const double B01 = fma(-u, sr[o + 14], sr[o + 17]);
+              const double Cax = fma(-u, sr[o + 6 + ax], sr[o + 0 + ax]);
+              const double Cpx = fma(u, sr[o + 9 + ax], sr[o + 3 + ax]);
+              const double I00 = (ax == 2) ? w * sr[o + 15] : 1.0;
+              const int gt = S_2D + ((j * 6 + ax) * N + n) * nI;
+              rys_2d1<double>(sr, gt, Le2, Lf2, I00, Cax, Cpx, B00, B10, B01);
+              if (ax == 2) {
+                const double w1 = sr[o + 18], w2 = sr[o + 19], w3 = sr[o + 20];
+                for (int i = 0; i < nI; ++i) {
+                  const double z = sr[gt + i];
+                  sr[gt + N * nI + i] = w1 * z;
+                  sr[gt + 2 * N * nI + i] = w2 * z;
+                  sr[gt + 3 * N * nI + i] = w3 * z;
+                }
+              }
+            }
+          }
+        } else {
+          for (int tk = tl; tk < bp * N; tk += TS) {
+            const int j = tk / N, n = tk - (tk / N) * N;
+            if (j < nbt) {
+              const int od = j * NPD, o = j * GNPR;
+              double u, w;
+              rys_root(a.rys_coef, a.rys_au, a.rys_aw, N, (int)__double_as_longlong(sd[od + 3]), sd[od + 0],
+                       sd[od + 1], sd[od + 2], n, u, w);
+              const double B00 = u * sr[o + 12];
+              const double B10 = fma(-u, sr[o + 13], sr[o + 16]);
+              const double B01 = fma(-u, sr[o + 14], sr[o + 17]);
+              const double wt = w * sr[o + 15];
+              const double C[3] = {fma(-u, sr[o + 6], sr[o + 0]), fma(-u, sr[o + 7], sr[o + 1]),
+                                   fma(-u, sr[o + 8], sr[o + 2])};
+              const double Cp[3] = {fma(u, sr[o + 9], sr[o + 3]), fma(u, sr[o + 10], sr[o + 4]),
+                                    fma(u, sr[o + 11], sr[o + 5])};
+              const int g0 = S_2D + ((j * 6 + 0) * N + n) * nI;
+              const int og[3] = {g0, g0 + N * nI, g0 + 2 * N * nI};
+              rys_2d3<double>(sr, og, Le2, Lf2, wt, C, Cp, B00, B10, B01);
+              // the I_z table scaled by the primitive weights 2 alpha, 2 beta, 2 gamma
+              const double w1 = sr[o + 18], w2 = sr[o + 19], w3 = sr[o + 20];
+              for (int i = 0; i < nI; ++i) {
+                const double z = sr[og[2] + i];
+                sr[og[2] + N * nI + i] = w1 * z;
+                sr[og[2] + 2 * N * nI + i] = w2 * z;
+                sr[og[2] + 3 * N * nI + i] = w3 * z;
+              }
             }
           }
         }

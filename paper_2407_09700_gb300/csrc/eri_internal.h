@@ -57,6 +57,7 @@ struct ClassDesc {
   int team_doubles_f32;  // shared-memory doubles per team (FP32 recurrences)
   int hrr_doubles;       // size of one HRR ping-pong buffer (doubles)
   long long scratch_per_team;  // global scratch doubles per team
+  int split3, split3_xy; // 1: the root phase runs (primitive, root, axis) items (batch bp / bp_xy)
   // Assembly of Eq. 1 by lane programs (every FP32 launch; FP64 launches with xy = 0): the
   // values sharing an I_x I_y product form groups; every lane of a team runs the same
   // sequence of group sizes, so slot k of a pass starts a group (one multiply) for all lanes
@@ -168,6 +169,7 @@ struct GradDesc {
   int nout;                                   // total assembled values (sum of the four sets)
   int nslot;                                  // lane-program slots (>= nout)
   int npass, bp, team_doubles;
+  int split3;                                 // 1: root phase over (primitive, root, axis) items
   int gam_off;                                // Gamma_J, Gamma_K: 2 * na nb nc nd doubles
   int hrr_off, hrr_doubles;                   // two HRR ping-pong buffers
   long long scratch_per_team;

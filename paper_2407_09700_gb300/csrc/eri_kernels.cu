@@ -344,26 +344,48 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : ((sizeof(R) == 4 && !XY) ?
           }
         }
         __syncwarp();
-        // ---- b. roots, weights (FP64) and 2D integrals (R) per (primitive, root)
-        for (int tk = tl; tk < bp * N; tk += TS) {
-          const int j = tk / N, n = tk - (tk / N) * N;
-          if (j < nbt) {
-            const int od = j * NPD, o = j * NPR;
-            double ud, wd;
-            rys_root(a.rys_coef, a.rys_au, a.rys_aw, N, (int)__double_as_longlong(sd[od + 3]), sd[od + 0],
-                     sd[od + 1], sd[od + 2], n, ud, wd);
-            const R u = (R)ud, w = (R)wd;
-            const R B00 = u * sr[o + 12];
-            const R B10 = fma(-u, sr[o + 13], sr[o + 16]);
-            const R B01 = fma(-u, sr[o + 14], sr[o + 17]);
-            const R wt = w * sr[o + 15];
-            const R C[3] = {fma(-u, sr[o + 6], sr[o + 0]), fma(-u, sr[o + 7], sr[o + 1]),
-                            fma(-u, sr[o + 8], sr[o + 2])};
-            const R Cp[3] = {fma(u, sr[o + 9], sr[o + 3]), fma(u, sr[o + 10], sr[o + 4]),
-                             fma(u, sr[o + 11], sr[o + 5])};
-            const int g0 = S_2D + ((j * 3 + 0) * N + n) * nI;
-            const int og[3] = {g0, g0 + N * nI, g0 + 2 * N * nI};
-            rys_2d3<R>(sr, og, Le, Lf, wt, C, Cp, B00, B10, B01);
+        // ---- b. roots, weights (FP64) and 2D integrals (R) per (primitive, root), or per
+        //      (primitive, root, axis) when that fills more of the team's lanes
+        if (TS > 1 && (XY ? c.split3_xy : c.split3)) {
+          for (int tk = tl; tk < bp * N * 3; tk += TS) {
+            const int jn = tk / 3, ax = tk - jn * 3;
+            const int j = jn / N, n = jn - (jn / N) * N;
+            if (j < nbt) {
+              const int od = j * NPD, o = j * NPR;
+              double ud, wd;
+              rys_root(a.rys_coef, a.rys_au, a.rys_aw, N, (int)__double_as_longlong(sd[od + 3]), sd[od + 0],
+                       sd[od + 1], sd[od + 2], n, ud, wd);
+              const R u = (R)ud;
+              const R B00 = u * sr[o + 12];
+              const R B10 = fma(-u, sr[o + 13], sr[o + 16]);
+              const R B01 = fma(-u, sr[o + 14], sr[o + 17]);
+              const R Cax = fma(-u, sr[o + 6 + ax], sr[o + 0 + ax]);
+              const R Cpx = fma(u, sr[o + 9 + ax], sr[o + 3 + ax]);
+              const R I00 = (ax == 2) ? (R)wd * sr[o + 15] : R(1);
+              rys_2d1<R>(sr, S_2D + ((j * 3 + ax) * N + n) * nI, Le, Lf, I00, Cax, Cpx, B00, B10, B01);
+            }
+          }
+        } else {
+          for (int tk = tl; tk < bp * N; tk += TS) {
+            const int j = tk / N, n = tk - (tk / N) * N;
+            if (j < nbt) {
+              const int od = j * NPD, o = j * NPR;
+              double ud, wd;
+              rys_root(a.rys_coef, a.rys_au, a.rys_aw, N, (int)__double_as_longlong(sd[od + 3]), sd[od + 0],
+                       sd[od + 1], sd[od + 2], n, ud, wd);
+              const R u = (R)ud, w = (R)wd;
+              const R B00 = u * sr[o + 12];
+              const R B10 = fma(-u, sr[o + 13], sr[o + 16]);
+              const R B01 = fma(-u, sr[o + 14], sr[o + 17]);
+              const R wt = w * sr[o + 15];
+              const R C[3] = {fma(-u, sr[o + 6], sr[o + 0]), fma(-u, sr[o + 7], sr[o + 1]),
+                              fma(-u, sr[o + 8], sr[o + 2])};
+              const R Cp[3] = {fma(u, sr[o + 9], sr[o + 3]), fma(u, sr[o + 10], sr[o + 4]),
+                               fma(u, sr[o + 11], sr[o + 5])};
+              const int g0 = S_2D + ((j * 3 + 0) * N + n) * nI;
+              const int og[3] = {g0, g0 + N * nI, g0 + 2 * N * nI};
+              rys_2d3<R>(sr, og, Le, Lf, wt, C, Cp, B00, B10, B01);
+            }
           }
         }
         __syncwarp();

@@ -207,6 +207,18 @@ void lane_programs(const std::vector<int>& key, int T, std::vector<int>* slot_va
   *slots_per_lane = Ls;
 }
 
+// Root phase of a batch: items (primitive, root) each evaluate the root polynomials and the
+// three axes' recurrences, or (split) items (primitive, root, axis) each evaluate the root
+// and one axis.  Split when it needs fewer lane iterations x item cost: it fills teams whose
+// bp N items leave lanes idle (high angular momentum, one primitive per batch).
+int choose_split3(int T, int bp, int N, int nI, int extra_z) {
+  if (T == 1) return 0;
+  const double root = 2.0 * RYS_DEG + 12.0, axis = 2.5 * nI;
+  const double whole = (double)((bp * N + T - 1) / T) * (root + 3 * axis + extra_z);
+  const double split = (double)((3 * bp * N + T - 1) / T) * (root + axis + extra_z);
+  return split < 0.9 * whole ? 1 : 0;
+}
+
 // Fill the static part of a class descriptor (no device pointers).  idx receives the
 // class's u32 tables: lane-program outidx [nslot], dst [nslot], gmask [npass], then (xy
 // classes) the shared-products tables xy_outidx [nout], xy_dst [nout], xytab [ncomb],
@@ -291,6 +303,7 @@ void make_class(int la, int lb, int lc, int ld, ClassDesc* c, int* ts, std::vect
   c->bp = (T == 1) ? 1 : std::max(1, std::min(32, team_budget(T) / per_prim));
   c->team_doubles = c->bp * per_prim;
   c->team_doubles_f32 = c->bp * 4 + (c->bp * (18 + 3 * c->nroots * c->nI) + 1) / 2;
+  c->split3 = choose_split3(T, c->bp, c->nroots, c->nI, 0);
   // Team regions of a block start an odd number of doubles apart, so the teams of a warp
   // reading the same table entry hit distinct shared-memory banks.
   if (T > 1) {
@@ -334,6 +347,7 @@ void make_class(int la, int lb, int lc, int ld, ClassDesc* c, int* ts, std::vect
       c->xymax = xymax;
       c->xysum_xy = xysum;
       c->bp_xy = bp_on;
+      c->split3_xy = choose_split3(T, bp_on, c->nroots, c->nI, 0);
       c->team_doubles_xy = (bp_on * per_prim + 2 * xymax) | 1;
       std::vector<uint32_t> outi(c->nout), dst(c->nout);
       for (int p = 0; p < xnp; ++p) {
@@ -435,6 +449,7 @@ void make_grad_class(int la, int lb, int lc, int ld, GradDesc* g, int* ts, std::
   }
   g->team_doubles = g->bp * per_prim;
   if (*ts > 1) g->team_doubles |= 1;      // odd team stride: distinct banks across teams
+  g->split3 = choose_split3(*ts, g->bp, g->nroots, g->nI, 3 * g->nI);
   const int nabcd = g->na * g->nb * g->nc * g->nd;
   g->gam_off = (off + 1) & ~1;
   g->hrr_off = g->gam_off + ((2 * nabcd + 1) & ~1);
