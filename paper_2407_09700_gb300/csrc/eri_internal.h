@@ -208,7 +208,7 @@ int erik_launch_rys(int N, int n, const double* T, double* u, double* w, const d
 int erik_probe_fma(double* fp64_tflops, double* fp32_tflops);
 // compile-time specialised kernels of the small classes (eri_small.cu)
 int erik_upload_cart_tables_small(void);
-int erik_small_available(int la, int lb, int lc, int ld);
+int erik_small_available(int la, int lb, int lc, int ld, int fp32);
 int erik_small_blocks_per_sm(int la, int lb, int lc, int ld, int fp32, int* out);
 int erik_launch_small(int la, int lb, int lc, int ld, int fp32, const struct KernelArgs* a, int grid, void* stream);
 // energy-gradient class kernels (eri_grad.cu)

@@ -130,8 +130,10 @@ ClassTune class_tune(int la, int lb, int lc, int ld) {
   }
   ClassTune t;
   // team sizes measured fastest on GB300 for the s/p/d classes of contracted 6-31G(d)-like
-  // shells (per-class CUDA-event times of the FP64 build, 1/2/4/8/32 lanes compared)
-  static const int measured[][5] = {{2, 1, 1, 0, 2}, {2, 2, 1, 0, 4}, {2, 0, 2, 0, 4}, {1, 1, 1, 1, 4}, {2, 2, 2, 1, 8}};
+  // shells (per-class CUDA-event times of the FP64 build, 1/2/4/8/32 lanes compared; 1 =
+  // the specialised one-lane kernel)
+  static const int measured[][5] = {{2, 1, 1, 0, 1}, {2, 0, 1, 1, 1}, {2, 0, 2, 0, 1}, {2, 2, 1, 0, 4},
+                                    {1, 1, 1, 1, 4}, {2, 2, 2, 1, 8}};
   for (const auto& m : measured)
     if (m[0] == la && m[1] == lb && m[2] == lc && m[3] == ld) t.ts = m[4];
   for (const auto& v : table)
@@ -832,7 +834,10 @@ eri_status plan_launches(eri_plan* p, size_t max_scratch, std::vector<Launch>* o
         eri_status s = launch_shape(p, X, Y, fp32, nt, &l.grid, &l.smem, &l.ts);
         if (s != ERI_OK) return s;
         const ClassDesc& cd = p->dev->classes[X][Y];
-        if (l.ts == 1 && erik_small_available(cd.la, cd.lb, cd.lc, cd.ld)) {
+        // specialised one-lane kernel: FP64 when the class runs with one lane per quartet,
+        // FP32 whenever one exists (its accumulators fit a lane in FP32)
+        if ((fp32 || l.ts == 1) && erik_small_available(cd.la, cd.lb, cd.lc, cd.ld, fp32)) {
+          l.ts = 1;
           int bps = 0;
           CUDA_TRY(erik_small_blocks_per_sm(cd.la, cd.lb, cd.lc, cd.ld, fp32, &bps));
           if (bps < 1) bps = 1;
@@ -1721,7 +1726,8 @@ eri_status eri_jk_batch(eri_batch* b, int njobs, eri_plan* const* plans, const d
       LL l{c.X, c.Y, fp32, 0, 0, 0, 0, c.total};
       if ((s = launch_shape(p0, c.X, c.Y, fp32, c.total, &l.grid, &l.smem, &l.ts)) != ERI_OK) return s;
       const ClassDesc& cd = p0->dev->classes[c.X][c.Y];
-      if (l.ts == 1 && erik_small_available(cd.la, cd.lb, cd.lc, cd.ld)) {
+      if ((fp32 || l.ts == 1) && erik_small_available(cd.la, cd.lb, cd.lc, cd.ld, fp32)) {
+        l.ts = 1;
         int bps = 0;
         CUDA_TRY(erik_small_blocks_per_sm(cd.la, cd.lb, cd.lc, cd.ld, fp32, &bps));
         l.grid = (int)std::max(1LL, std::min((long long)p0->dev->sms * std::max(bps, 1), (c.total + 127) / 128));

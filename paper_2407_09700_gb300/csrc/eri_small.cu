@@ -1,11 +1,11 @@
 // Compile-time specialised Rys kernels for the low angular-momentum classes whose
-// contracted [e0|f0] block has at most 32 values (the classes run with one lane per
-// shell quartet).  Following Sec. 3's design for small root counts (Alg. 2: unrolled
-// recurrences, intermediates in registers, contraction before digestion), every loop
-// here has compile-time bounds: the 2D tables I_x, I_y, I_z of one root and the
-// contracted accumulators live in registers and the Eq. 1 index map is folded into the
-// code.  Task fetching, screening, the transfer relations and the digestion are the
-// shared device functions of eri_device.cuh.
+// contracted [e0|f0] block fits a lane's registers (up to 54 values in FP64, 96 in the
+// FP32 path of the mixed mode); each runs with one lane per shell quartet.  Following
+// Sec. 3's design for small root counts (Alg. 2: unrolled recurrences, intermediates in
+// registers, contraction before digestion), every loop here has compile-time bounds: the
+// 2D tables I_x, I_y, I_z of one root and the contracted accumulators live in registers
+// and the Eq. 1 index map is folded into the code.  Task fetching, screening, the
+// transfer relations and the digestion are the shared device functions of eri_device.cuh.
 #include <type_traits>
 
 #include "eri_device.cuh"
@@ -49,7 +49,7 @@ struct Small {
 };
 
 template <int LA, int LB, int LC, int LD, typename R>
-__global__ void __launch_bounds__(TPB, 3) eri_small_kernel(const KernelArgs a) {
+__global__ void __launch_bounds__(TPB, (Small<LA, LB, LC, LD>::NOUT > 32 ? 2 : 3)) eri_small_kernel(const KernelArgs a) {
   using S = Small<LA, LB, LC, LD>;
   typedef typename PairOf<R>::type PP;
   constexpr int LE = S::LE, LF = S::LF, L1 = S::L1, NI = S::NI, N = S::N, NOUT = S::NOUT;
@@ -208,7 +208,12 @@ __global__ void __launch_bounds__(TPB, 3) eri_small_kernel(const KernelArgs a) {
 // (la lb | lc ld) of the specialised classes and their kernels
 #define SMALL_CLASSES(X)                                                                       \
   X(0, 0, 0, 0) X(1, 0, 0, 0) X(1, 1, 0, 0) X(2, 0, 0, 0) X(2, 1, 0, 0) X(2, 2, 0, 0)           \
-  X(3, 0, 0, 0) X(3, 1, 0, 0) X(4, 0, 0, 0) X(1, 0, 1, 0) X(1, 1, 1, 0) X(2, 0, 1, 0) X(3, 0, 1, 0)
+  X(3, 0, 0, 0) X(3, 1, 0, 0) X(4, 0, 0, 0) X(1, 0, 1, 0) X(1, 1, 1, 0) X(2, 0, 1, 0) X(3, 0, 1, 0)      \
+  X(2, 1, 1, 0) X(2, 0, 2, 0) X(2, 0, 1, 1)
+
+// classes whose accumulators fit a lane's registers only in FP32: specialised for the FP32
+// path of the mixed mode, team kernels for FP64
+#define SMALL_CLASSES_F32(X) X(1, 1, 1, 1) X(2, 1, 2, 0) X(2, 2, 1, 0)
 
 const void* small_ptr(int la, int lb, int lc, int ld, int fp32) {
 #define SMALL_CASE(A, B, C, D)                                                   \
@@ -217,6 +222,10 @@ const void* small_ptr(int la, int lb, int lc, int ld, int fp32) {
                 : (const void*)eri_small_kernel<A, B, C, D, double>;
   SMALL_CLASSES(SMALL_CASE)
 #undef SMALL_CASE
+#define SMALL_CASE_F32(A, B, C, D)                                               \
+  if (fp32 && la == A && lb == B && lc == C && ld == D) return (const void*)eri_small_kernel<A, B, C, D, float>;
+  SMALL_CLASSES_F32(SMALL_CASE_F32)
+#undef SMALL_CASE_F32
   return nullptr;
 }
 
@@ -234,8 +243,10 @@ extern "C" int erik_upload_cart_tables_small(void) {
   return (int)cudaMemcpyToSymbol(c_cart, h, sizeof(h));
 }
 
-// 1 if (la lb | lc ld) has a specialised kernel.
-extern "C" int erik_small_available(int la, int lb, int lc, int ld) { return small_ptr(la, lb, lc, ld, 0) != nullptr; }
+// 1 if (la lb | lc ld) has a specialised kernel for this precision (fp32 = 1: FP32 path).
+extern "C" int erik_small_available(int la, int lb, int lc, int ld, int fp32) {
+  return small_ptr(la, lb, lc, ld, fp32) != nullptr;
+}
 
 extern "C" int erik_small_blocks_per_sm(int la, int lb, int lc, int ld, int fp32, int* out) {
   const void* k = small_ptr(la, lb, lc, ld, fp32);
@@ -255,5 +266,12 @@ extern "C" int erik_launch_small(int la, int lb, int lc, int ld, int fp32, const
   }
   SMALL_CLASSES(SMALL_LAUNCH)
 #undef SMALL_LAUNCH
+#define SMALL_LAUNCH_F32(A, B, C, D)                                                          \
+  if (fp32 && la == A && lb == B && lc == C && ld == D) {                                     \
+    eri_small_kernel<A, B, C, D, float><<<grid, TPB, 0, s>>>(*a);                             \
+    return (int)cudaGetLastError();                                                           \
+  }
+  SMALL_CLASSES_F32(SMALL_LAUNCH_F32)
+#undef SMALL_LAUNCH_F32
   return (int)cudaErrorInvalidValue;
 }
