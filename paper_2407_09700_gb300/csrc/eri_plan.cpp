@@ -664,6 +664,10 @@ struct eri_plan {
   unsigned* d_tiles = nullptr;                // per-tile counts / offsets of the compaction
   unsigned long long* d_gstats = nullptr;     // [2] quartets / primitive quartets of eri_jk_grad
   cudaStream_t grad_stream = nullptr;
+  // second stream of eri_jk: classes alternate between the caller's stream and this one,
+  // each with its own half of the task lists, tile counts and scratch
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   size_t tiles_cap = 0;
   size_t host_io_cap = 0;
   cudaStream_t last_stream = nullptr;
@@ -866,8 +870,14 @@ eri_status plan_launches(eri_plan* p, size_t max_scratch, std::vector<Launch>* o
 
 // Density maxima, every class launch, symmetrisation.  Records launches for the profiler
 // when record is set.  Allocates nothing except profiling events when record is set.
+// With two streams (nstreams = 2) the class launches alternate between st and the plan's
+// side stream, so one class's launch fills the SMs that the previous class's tail leaves
+// idle; stream s uses task list d_tlist + s * list_half, tile counts d_tiles + s *
+// tiles_half and scratch + s * scratch_half.  Per-launch profiling forces one stream so
+// that each launch's events time it alone.
 eri_status run_jk(eri_plan* p, const std::vector<Launch>& launches, const double* D, int nD, double* J, double* K,
-                  int want, cudaStream_t st, double* scratch, bool record, bool use_lists) {
+                  int want, cudaStream_t st, double* scratch, bool record, bool use_lists, int nstreams = 1,
+                  size_t list_half = 0, size_t tiles_half = 0, size_t scratch_half = 0) {
   const size_t mat = (size_t)nD * p->nbf * p->nbf;
   if (want & 1) CUDA_TRY(cudaMemsetAsync(J, 0, sizeof(double) * mat, st));
   if (want & 2) CUDA_TRY(cudaMemsetAsync(K, 0, sizeof(double) * mat, st));
@@ -876,6 +886,16 @@ eri_status run_jk(eri_plan* p, const std::vector<Launch>& launches, const double
   CUDA_TRY(cudaMemsetAsync(p->d_stats, 0, sizeof(unsigned long long) * 4 * 256, st));
   if (use_lists) CUDA_TRY(cudaMemsetAsync(p->d_tcount, 0, sizeof(unsigned long long) * 2 * 256, st));
   const bool prof = record && p->profiling;
+  if (prof) nstreams = 1;
+  cudaStream_t ss[2] = {st, st};
+  if (nstreams == 2) {
+    if (!p->side) {
+      CUDA_TRY(cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking));
+      CUDA_TRY(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
+      CUDA_TRY(cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming));
+    }
+    ss[1] = p->side;
+  }
   if (prof) {
     while (p->events.size() < 2 * launches.size()) {
       cudaEvent_t e;
@@ -890,11 +910,20 @@ eri_status run_jk(eri_plan* p, const std::vector<Launch>& launches, const double
     p->last_launch_fp32.clear();
     p->last_launch_small.clear();
   }
+  if (nstreams == 2) {
+    CUDA_TRY(cudaEventRecord(p->ev_fork, st));
+    CUDA_TRY(cudaStreamWaitEvent(p->side, p->ev_fork, 0));
+  }
+  const size_t list_cap = nstreams == 2 ? list_half : p->tlist_cap;
   long long cand = 0;
   int li = 0, ci = -1;
   const bool mixed = p->opts.precision == ERI_MIXED;
   for (const Launch& l : launches) {
-    const bool listed = use_lists && (unsigned long long)l.nt <= 0xffffffffULL && (size_t)l.nt <= p->tlist_cap;
+    const bool listed = use_lists && (unsigned long long)l.nt <= 0xffffffffULL && (size_t)l.nt <= list_cap;
+    const int sidx = (nstreams == 2) ? ((ci + (l.fp32 ? 0 : 1)) & 1) : 0;
+    const cudaStream_t sl = ss[sidx];
+    unsigned* tlist_l = p->d_tlist + (size_t)sidx * list_half;
+    unsigned* tiles_l = p->d_tiles + (size_t)sidx * tiles_half;
     KernelArgs a = base_args(p, l.X, l.Y);
     a.pairs = p->d_pairs;
     a.bra0 = p->type_off[l.X];
@@ -914,24 +943,24 @@ eri_status run_jk(eri_plan* p, const std::vector<Launch>& launches, const double
     a.want = want;
     a.mode = KMODE_JK;
     a.counter = p->d_counters + li;
-    a.scratch = scratch;
+    a.scratch = scratch + (size_t)sidx * scratch_half;
     a.stats = p->d_stats + 2 * (256 * l.fp32 + l.X * ERI_NPAIRTYPE + l.Y);
     if (!l.fp32) ++ci;
     if (listed) {
       unsigned long long* cnt = p->d_tcount + 2 * ci;
       if (!l.fp32)
-        CUDA_TRY(erik_launch_compact(&a, p->d_tlist, (unsigned long long)l.nt, cnt, p->d_tiles, mixed ? 1 : 0, st));
-      a.tlist = p->d_tlist;
+        CUDA_TRY(erik_launch_compact(&a, tlist_l, (unsigned long long)l.nt, cnt, tiles_l, mixed ? 1 : 0, sl));
+      a.tlist = tlist_l;
       a.list_cap = (unsigned long long)l.nt;
       a.from_back = l.fp32;
       a.tcount = cnt + l.fp32;
     }
-    if (prof) CUDA_TRY(cudaEventRecord(p->events[2 * li], st));
+    if (prof) CUDA_TRY(cudaEventRecord(p->events[2 * li], sl));
     if (l.small)
-      CUDA_TRY(erik_launch_small(a.c.la, a.c.lb, a.c.lc, a.c.ld, l.fp32, &a, l.grid, st));
+      CUDA_TRY(erik_launch_small(a.c.la, a.c.lb, a.c.lc, a.c.ld, l.fp32, &a, l.grid, sl));
     else
-      CUDA_TRY(erik_launch_class(l.ts, l.fp32, &a, l.grid, l.smem, st));
-    if (prof) CUDA_TRY(cudaEventRecord(p->events[2 * li + 1], st));
+      CUDA_TRY(erik_launch_class(l.ts, l.fp32, &a, l.grid, l.smem, sl));
+    if (prof) CUDA_TRY(cudaEventRecord(p->events[2 * li + 1], sl));
     if (record) {
       p->last_launch_xy.push_back(l.X * ERI_NPAIRTYPE + l.Y);
       p->last_launch_ts.push_back(l.ts);
@@ -941,6 +970,10 @@ eri_status run_jk(eri_plan* p, const std::vector<Launch>& launches, const double
     }
     if (!l.fp32) cand += l.nt;
     ++li;
+  }
+  if (nstreams == 2) {
+    CUDA_TRY(cudaEventRecord(p->ev_join, p->side));
+    CUDA_TRY(cudaStreamWaitEvent(st, p->ev_join, 0));
   }
   if (want & 1) CUDA_TRY(erik_launch_symmetrize(J, nD, p->nbf, st));
   if (want & 2) CUDA_TRY(erik_launch_symmetrize(K, nD, p->nbf, st));
@@ -965,6 +998,9 @@ eri_status eri_plan_destroy(eri_plan* p) {
   cudaSetDevice(p->device);
   cudaDeviceSynchronize();
   for (cudaEvent_t e : p->events) cudaEventDestroy(e);
+  if (p->side) cudaStreamDestroy(p->side);
+  if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+  if (p->ev_join) cudaEventDestroy(p->ev_join);
   void* bufs[] = {p->d_pairs_all, p->d_pairs, p->d_prims, p->d_primsf, p->d_sh_bf0, p->d_sh_n, p->d_sh_atom, p->d_Dmax, p->d_counters,
                   p->d_stats, p->d_scratch, p->d_tasks, p->d_out, p->d_off, p->d_host_io, p->d_tlist,
                   p->d_tcount, p->d_tiles, p->d_gstats};
@@ -1185,13 +1221,18 @@ eri_status eri_jk(eri_plan* p, const double* D, int nD, double* J, double* K, in
   size_t need = 0;
   for (const Launch& l : launches)
     need = std::max(need, (size_t)l.grid * (size_t)(128 / l.ts) * (size_t)p->dev->classes[l.X][l.Y].scratch_per_team);
-  if ((s = ensure_scratch(p, need)) != ERI_OK) return s;
+  need = (need + 31) & ~(size_t)31;
   size_t maxnt = 1;
   for (const Launch& l : launches)
     if ((unsigned long long)l.nt <= 0xffffffffULL) maxnt = std::max(maxnt, (size_t)l.nt);
-  if ((s = ensure_buf(&p->d_tlist, &p->tlist_cap, maxnt)) != ERI_OK) return s;
-  if ((s = ensure_buf(&p->d_tiles, &p->tiles_cap, 2 * ((maxnt + 1023) / 1024 + 1))) != ERI_OK) return s;
-  return run_jk(p, launches, D, nD, J, K, flags & 3, (cudaStream_t)cuda_stream, p->d_scratch, true, true);
+  maxnt = (maxnt + 31) & ~(size_t)31;
+  const size_t tiles = 2 * ((maxnt + 1023) / 1024 + 1);
+  // two streams, each with its own half of scratch, task lists and tile counts
+  if ((s = ensure_scratch(p, 2 * need)) != ERI_OK) return s;
+  if ((s = ensure_buf(&p->d_tlist, &p->tlist_cap, 2 * maxnt)) != ERI_OK) return s;
+  if ((s = ensure_buf(&p->d_tiles, &p->tiles_cap, 2 * tiles)) != ERI_OK) return s;
+  return run_jk(p, launches, D, nD, J, K, flags & 3, (cudaStream_t)cuda_stream, p->d_scratch, true, true, 2, maxnt,
+                tiles, need);
 }
 
 eri_status eri_jk_grad(eri_plan* p, const double* D, double* gJ, double* gK, void* cuda_stream) {
