@@ -279,7 +279,9 @@ def run_ours(args):
     nsteps_total = args.steps * ws
     value = nsteps_total / t_max
     quartets_per_s = st["quartets_computed"] * nsteps_total / t_max
-    launches_per_step = 1 + st["nclasses_launched"] + 2
+    # per build: the density-maxima kernel, the class kernels, three compaction kernels
+    # (counts, scan, ordered writes) per FP64 class launch, and the two symmetrisations
+    launches_per_step = 1 + st["nclasses_launched"] + 3 * st["nclasses_launched"] + 2
 
     # dominant kernel: the class-kernel instantiation with the most time in the region
     dom_name, dom = max(per_kernel.items(), key=lambda kv: kv[1]["ms"])
