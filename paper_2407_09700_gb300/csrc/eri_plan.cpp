@@ -1266,19 +1266,35 @@ eri_status eri_jk_grad(eri_plan* p, const double* D, double* gJ, double* gK, voi
     }
   }
   eri_status s;
-  if ((s = ensure_scratch(p, need)) != ERI_OK) return s;
-  if ((s = ensure_buf(&p->d_tlist, &p->tlist_cap, maxnt)) != ERI_OK) return s;
-  if ((s = ensure_buf(&p->d_tiles, &p->tiles_cap, 2 * ((maxnt + 1023) / 1024 + 1))) != ERI_OK) return s;
+  // two streams, as in eri_jk: each with its own half of scratch, task lists and tile counts
+  need = (need + 31) & ~(size_t)31;
+  maxnt = (maxnt + 31) & ~(size_t)31;
+  const size_t tiles = 2 * ((maxnt + 1023) / 1024 + 1);
+  if ((s = ensure_scratch(p, 2 * need)) != ERI_OK) return s;
+  if ((s = ensure_buf(&p->d_tlist, &p->tlist_cap, 2 * maxnt)) != ERI_OK) return s;
+  if ((s = ensure_buf(&p->d_tiles, &p->tiles_cap, 2 * tiles)) != ERI_OK) return s;
   if (!p->d_gstats) CUDA_TRY(cudaMalloc(&p->d_gstats, sizeof(unsigned long long) * 2));
+  if (!p->side) {
+    CUDA_TRY(cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking));
+    CUDA_TRY(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
+    CUDA_TRY(cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming));
+  }
+  const cudaStream_t ss[2] = {st, p->side};
   CUDA_TRY(cudaMemsetAsync(gJ, 0, sizeof(double) * 3 * p->natm, st));
   CUDA_TRY(cudaMemsetAsync(gK, 0, sizeof(double) * 3 * p->natm, st));
   CUDA_TRY(cudaMemsetAsync(p->d_gstats, 0, sizeof(unsigned long long) * 2, st));
   CUDA_TRY(erik_launch_dmax(D, 1, p->nbf, p->nshell, p->d_sh_bf0, p->d_sh_n, p->d_Dmax, st));
   CUDA_TRY(cudaMemsetAsync(p->d_counters, 0, sizeof(unsigned long long) * 256, st));
   CUDA_TRY(cudaMemsetAsync(p->d_tcount, 0, sizeof(unsigned long long) * 2 * 256, st));
+  CUDA_TRY(cudaEventRecord(p->ev_fork, st));
+  CUDA_TRY(cudaStreamWaitEvent(p->side, p->ev_fork, 0));
   int li = 0;
   for (const GL& l : ls) {
     const GradDesc& g = p->dev->gclasses[l.X][l.Y];
+    const int sidx = li & 1;
+    const cudaStream_t sl = ss[sidx];
+    unsigned* tlist_l = p->d_tlist + (size_t)sidx * maxnt;
+    unsigned* tiles_l = p->d_tiles + (size_t)sidx * tiles;
     KernelArgs a = base_args(p, l.X, l.Y);
     const int N = g.nroots;
     a.rys_coef = p->dev->rys_coef + RYS_COEF_OFFSET[N];
@@ -1301,11 +1317,11 @@ eri_status eri_jk_grad(eri_plan* p, const double* D, double* gJ, double* gK, voi
     a.want = 3;
     a.mode = KMODE_JK;
     a.counter = p->d_counters + li;
-    a.scratch = p->d_scratch;
+    a.scratch = p->d_scratch + (size_t)sidx * need;
     a.stats = p->d_gstats;
     unsigned long long* cnt = p->d_tcount + 2 * li;
-    CUDA_TRY(erik_launch_compact(&a, p->d_tlist, (unsigned long long)l.nt, cnt, p->d_tiles, 0, st));
-    a.tlist = p->d_tlist;
+    CUDA_TRY(erik_launch_compact(&a, tlist_l, (unsigned long long)l.nt, cnt, tiles_l, 0, sl));
+    a.tlist = tlist_l;
     a.list_cap = (unsigned long long)l.nt;
     a.from_back = 0;
     a.tcount = cnt;
@@ -1316,9 +1332,11 @@ eri_status eri_jk_grad(eri_plan* p, const double* D, double* gJ, double* gK, voi
     ga.sh_atom = p->d_sh_atom;
     ga.gJ = gJ;
     ga.gK = gK;
-    CUDA_TRY(erik_launch_grad(l.ts, &ga, l.grid, l.smem, st));
+    CUDA_TRY(erik_launch_grad(l.ts, &ga, l.grid, l.smem, sl));
     ++li;
   }
+  CUDA_TRY(cudaEventRecord(p->ev_join, p->side));
+  CUDA_TRY(cudaStreamWaitEvent(st, p->ev_join, 0));
   p->grad_stream = st;
   return ERI_OK;
 }
