@@ -192,7 +192,6 @@ struct GradArgs {
 extern "C" {
 #endif
 int erik_upload_cart_tables(void);
-int erik_team_config(int ts, int* threads_per_block, int* max_g);
 int erik_blocks_per_sm(int ts, int fp32, int xy, int smem_bytes, int* out);
 int erik_launch_class(int ts, int fp32, const struct KernelArgs* a, int grid, int smem_bytes, void* stream);
 int erik_launch_compact(const struct KernelArgs* a, unsigned* tlist, unsigned long long cap,

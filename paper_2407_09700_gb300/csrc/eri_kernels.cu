@@ -553,12 +553,6 @@ extern "C" int erik_upload_cart_tables(void) {
   return (int)cudaMemcpyToSymbol(c_cart, h, sizeof(h));
 }
 
-extern "C" int erik_team_config(int ts, int* threads_per_block, int* max_g) {
-  *threads_per_block = TPB;
-  *max_g = GSLOTS;
-  return (ts == 1 || ts == 2 || ts == 4 || ts == 8 || ts == 32) ? 0 : 1;
-}
-
 static const void* class_kernel_ptr(int ts, int fp32, int xy) {
   if (fp32) {
     switch (ts * 2 + (xy ? 1 : 0)) {

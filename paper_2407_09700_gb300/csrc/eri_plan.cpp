@@ -590,13 +590,6 @@ void class_model_flops2(const ClassDesc& c, int nD, int want, int fp32, double* 
   }
 }
 
-void class_model_flops(const ClassDesc& c, int nD, int want, double* per_prim, double* per_quartet) {
-  double a, b, q, r;
-  class_model_flops2(c, nD, want, 0, &a, &b, &q, &r);
-  *per_prim = a + b;
-  *per_quartet = q + r;
-}
-
 void normalise(int nshell, const int* l, const int* nprim, const int* off, const double* exps,
                const double* raw, std::vector<double>& out) {
   for (int s = 0; s < nshell; ++s) {
