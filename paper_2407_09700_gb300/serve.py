@@ -69,7 +69,10 @@ def _percentile(x, q):
 
 class Server:
     def __init__(self, precision: int = ERI_MIXED, mixed_thresh: float = 1e-5, hbm_budget: int = 8 << 30,
-                 max_slots: int = 32, scf_conv: float = 1e-8, scf_max_iter: int = 100):
+                 max_slots: int = 32, scf_conv: float = 1e-8, scf_max_iter: int = 100, batch=None, sync=None):
+        """batch: the batched J/K engine (an eri_batch by default); sync: waits for the device
+        (torch.cuda.synchronize by default).  Both are replaceable so that the admission and
+        retirement policy can run against stand-ins."""
         import torch
         self.torch = torch
         self.precision = precision
@@ -78,9 +81,12 @@ class Server:
         self.max_slots = max_slots
         self.scf_conv = scf_conv
         self.scf_max_iter = scf_max_iter
-        self.batch = Batch()
+        self.batch = batch if batch is not None else Batch()
+        self.sync = sync if sync is not None else torch.cuda.synchronize
         self.ticks = 0
         self.batch_sizes: List[int] = []
+        self.max_active = 0
+        self.max_used = 0
 
     def _admit(self, job: Job, now: float):
         torch = self.torch
@@ -120,6 +126,8 @@ class Server:
                 self._admit(j, now)
                 active.append(j)
                 used += j.footprint
+                self.max_active = max(self.max_active, len(active))
+                self.max_used = max(self.max_used, used)
             if not active:
                 if pending:
                     if pending[0].footprint > self.hbm_budget:
@@ -146,7 +154,7 @@ class Server:
                     else:
                         j.D = j.scf.D.unsqueeze(0).contiguous()
             if done:
-                torch.cuda.synchronize()
+                self.sync()
                 now = time.perf_counter() - t0
                 for j in done:
                     self._retire(j, now)

@@ -1,0 +1,124 @@
+"""Host-side logic without a GPU: the bench's multi-rank plumbing on two gloo ranks
+(barrier, max over ranks, replica throughput) and the server's continuous-batching
+policy (admission by slots and HBM footprint, requests admitted while others run,
+retirement, latency summary) driven by stand-in jobs."""
+
+import math
+import os
+import socket
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, ws, port, q):
+    os.environ.update(RANK=str(rank), WORLD_SIZE=str(ws), LOCAL_RANK=str(rank), MASTER_ADDR="127.0.0.1",
+                      MASTER_PORT=str(port))
+    import bench
+    d = bench.Dist("gloo")
+    d.barrier()
+    t = 0.25 * (rank + 1)                      # each rank's timed region
+    t_max = d.max(t)
+    q.put((rank, t_max, bench.replica_throughput(3, ws, t_max)))
+    d.barrier()
+    d.close()
+
+
+def test_two_gloo_ranks_barrier_and_max():
+    ctx = torch.multiprocessing.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert [o[1] for o in out] == [0.5, 0.5]            # both ranks see the slowest rank's time
+    assert all(o[2] == pytest.approx(3 * 2 / 0.5) for o in out)
+
+
+# ---------------------------------------------------------------- server policy with stand-ins
+
+class _FakeBatch:
+    def __init__(self, delay):
+        self.calls = []
+        self.delay = delay
+
+    def jk(self, plans, Ds, Js, Ks):
+        import time
+        self.calls.append(len(plans))
+        time.sleep(self.delay)
+
+
+class _FakeSCF:
+    def __init__(self, iters):
+        self.left = iters
+        self.D = torch.zeros(1)
+
+    def update(self, J, K, conv):
+        self.left -= 1
+        return -1.0, self.left <= 0
+
+
+def _server(**kw):
+    from paper_2407_09700_gb300.serve import Server
+
+    class S(Server):
+        def _admit(self, job, now):
+            job.plan = object()
+            job.scf = _FakeSCF(job.mol) if job.kind == "scf" else None
+            job.D = job.J = job.K = torch.zeros((1, 1, 1))
+            job.admit = now
+
+        def _retire(self, job, now):
+            job.finish = now
+            job.plan = job.scf = None
+
+    return S(batch=_FakeBatch(kw.pop("delay", 0.002)), sync=lambda: None, **kw)
+
+
+def _jobs(spec):
+    from paper_2407_09700_gb300.serve import Job
+    return [Job(rid=i, kind=k, mol=it, arrival=a, footprint=f) for i, (k, it, a, f) in enumerate(spec)]
+
+
+def test_server_admits_by_slots_and_footprint():
+    # 6 J/K requests at t = 0 of footprint 4; budget 10 and 3 slots -> at most 2 together
+    jobs = _jobs([("jk", 0, 0.0, 4)] * 6)
+    srv = _server(hbm_budget=10, max_slots=3)
+    out = srv.run(jobs)
+    assert srv.max_active == 2 and srv.max_used <= 10
+    assert srv.batch.calls == [2, 2, 2]
+    assert out["requests"] == 6 and all(j.finish >= j.admit >= j.arrival for j in jobs)
+
+
+def test_server_continuous_admission_and_latency():
+    # a long RHF job (10 ticks) is running when J/K requests arrive: they are admitted into
+    # the running batch and finish long before it
+    jobs = _jobs([("scf", 10, 0.0, 1)] + [("jk", 0, 0.005 * (i + 1), 1) for i in range(4)])
+    srv = _server(hbm_budget=100, max_slots=8, delay=0.004)
+    out = srv.run(jobs)
+    scf, jks = jobs[0], jobs[1:]
+    assert srv.ticks == 10
+    assert max(srv.batch.calls) >= 2                       # the J/K requests shared ticks with the RHF job
+    assert all(j.finish < scf.finish for j in jks)
+    lat = sorted(j.finish - j.arrival for j in jobs)
+    assert out["p50_latency_s"] == pytest.approx(float(np.percentile(lat, 50)))
+    assert out["p99_latency_s"] == pytest.approx(float(np.percentile(lat, 99)))
+    assert math.isfinite(out["throughput_req_s"]) and out["throughput_req_s"] > 0
+
+
+def test_server_rejects_a_request_larger_than_the_budget():
+    jobs = _jobs([("jk", 0, 0.0, 50)])
+    with pytest.raises(RuntimeError, match="exceeds the HBM budget"):
+        _server(hbm_budget=10, max_slots=2).run(jobs)
