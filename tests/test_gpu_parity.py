@@ -305,3 +305,60 @@ def test_jk_team_size_overrides(tmp_path, cfg):
         J, K = (np.array(x).reshape(Jr.shape) for x in out[name])
         assert np.abs(J - Jr).max() <= tol, (name, np.abs(J - Jr).max())
         assert np.abs(K - Kr).max() <= tol, (name, np.abs(K - Kr).max())
+
+
+# ---------------------------------------------------------------- full-size workloads, sampled outputs
+
+def _sample_pairs(m, n, seed):
+    """Shell pairs (I, X) for sampled J / K blocks: n random ones plus, for every pair of
+    angular momenta present, one pair with those momenta."""
+    rng = np.random.default_rng(seed)
+    ns = m.nshell
+    pairs = [(int(rng.integers(ns)), int(rng.integers(ns))) for _ in range(n)]
+    seen = set()
+    for i in rng.permutation(ns):
+        for x in rng.permutation(ns)[:8]:
+            key = (int(m.shell_l[i]), int(m.shell_l[x]))
+            if key not in seen:
+                seen.add(key)
+                pairs.append((int(i), int(x)))
+    return pairs
+
+
+_FULL = {}
+
+
+def _full_case(name):
+    """The benchmark's workloads at full size with oracle J / K blocks on sampled shell
+    pairs (computed once per module)."""
+    if name not in _FULL:
+        m = config_medium(seed=0) if name == "medium" else config_high_l(seed=0)
+        pairs = _sample_pairs(m, 4, seed=11)
+        Jl, Kl = oracle.jk_blocks(m, pairs)
+        _FULL[name] = (m, pairs, Jl, Kl)
+    return _FULL[name]
+
+
+def _check_blocks(m, pairs, Jl, Kl, J, K, tol):
+    f0 = m.shell_first_bf()
+    nf = [(int(l) + 1) * (int(l) + 2) // 2 for l in m.shell_l]
+    worst = 0.0
+    for (i, x), Jb, Kb in zip(pairs, Jl, Kl):
+        gJ = J[:, f0[i]:f0[i] + nf[i], f0[x]:f0[x] + nf[x]]
+        gK = K[:, f0[i]:f0[i] + nf[i], f0[x]:f0[x] + nf[x]]
+        worst = max(worst, float(np.abs(gJ - Jb).max()), float(np.abs(gK - Kb).max()))
+    assert worst <= tol, worst
+
+
+@pytest.mark.parametrize("name,precision,tol", [("medium", pkg.ERI_FP64, 1e-10), ("medium", pkg.ERI_MIXED, 1e-6),
+                                                ("high_l", pkg.ERI_FP64, 1e-10)])
+def test_jk_full_size_sampled_blocks(name, precision, tol):
+    """The 30-atom medium build the benchmark times (and the 12-atom s..g build) through
+    eri_jk in its launch configuration, against oracle J / K blocks on sampled shell pairs
+    covering every pair of angular momenta; the mixed build at the bench's split 1e-5."""
+    m, pairs, Jl, Kl = _full_case(name)
+    plan = pkg.Plan(m, precision=precision, mixed_thresh=1e-5)
+    J, K = _jk_gpu(plan, m.D)
+    _check_blocks(m, pairs, Jl, Kl, J, K, tol)
+    st = plan.stats()
+    assert st["quartets_computed"] > 0
