@@ -1667,7 +1667,7 @@ struct eri_batch {
   size_t blist_cap = 0;
   unsigned* d_tiles = nullptr;
   size_t tiles_cap = 0;
-  unsigned long long* d_small = nullptr;     // counts[2], base[2]
+  unsigned long long* d_small = nullptr;     // per stream: counts[2], base[2]
   unsigned long long* d_cursor = nullptr;    // [256][2]
   unsigned long long* d_counter = nullptr;   // [512]
   unsigned long long* d_stats = nullptr;     // [2][256][2]
@@ -1676,6 +1676,10 @@ struct eri_batch {
   cudaStream_t last_stream = nullptr;
   long long last_quartets = 0;
   int last_launches = 0;
+  // second stream: classes alternate between the caller's stream and this one, each with
+  // its own half of the merged lists, tile counts, small counters and scratch
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 extern "C" {
@@ -1692,7 +1696,7 @@ eri_status eri_batch_create(eri_batch** out) {
   eri_batch* b = new (std::nothrow) eri_batch();
   if (!b) return fail(ERI_ERR_OOM, "host allocation failed");
   cudaGetDevice(&b->device);
-  if (cudaMalloc(&b->d_small, sizeof(unsigned long long) * 4) != cudaSuccess ||
+  if (cudaMalloc(&b->d_small, sizeof(unsigned long long) * 8) != cudaSuccess ||
       cudaMalloc(&b->d_cursor, sizeof(unsigned long long) * 2 * 256) != cudaSuccess ||
       cudaMalloc(&b->d_counter, sizeof(unsigned long long) * 512) != cudaSuccess ||
       cudaMalloc(&b->d_stats, sizeof(unsigned long long) * 4 * 256) != cudaSuccess) {
@@ -1712,6 +1716,9 @@ eri_status eri_batch_destroy(eri_batch* b) {
   void* bufs[] = {b->d_jobs, b->d_blist, b->d_tiles, b->d_small, b->d_cursor, b->d_counter, b->d_stats, b->d_scratch};
   for (void* x : bufs)
     if (x) cudaFree(x);
+  if (b->side) cudaStreamDestroy(b->side);
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+  if (b->ev_join) cudaEventDestroy(b->ev_join);
   delete b;
   return ERI_OK;
 }
@@ -1790,18 +1797,27 @@ eri_status eri_jk_batch(eri_batch* b, int njobs, eri_plan* const* plans, const d
       launches.push_back(l);
     }
   }
-  if ((s = ensure_buf(&b->d_blist, &b->blist_cap, cap)) != ERI_OK) return s;
-  if ((s = ensure_buf(&b->d_tiles, &b->tiles_cap, tcap)) != ERI_OK) return s;
-  if (need > b->scratch_doubles) {
+  cap = (cap + 31) & ~(size_t)31;
+  tcap = (tcap + 31) & ~(size_t)31;
+  need = (need + 31) & ~(size_t)31;
+  if ((s = ensure_buf(&b->d_blist, &b->blist_cap, 2 * cap)) != ERI_OK) return s;
+  if ((s = ensure_buf(&b->d_tiles, &b->tiles_cap, 2 * tcap)) != ERI_OK) return s;
+  if (2 * need > b->scratch_doubles) {
     if (b->d_scratch) {
       CUDA_TRY(cudaDeviceSynchronize());
       cudaFree(b->d_scratch);
       b->d_scratch = nullptr;
       b->scratch_doubles = 0;
     }
-    CUDA_TRY(cudaMalloc(&b->d_scratch, sizeof(double) * need));
-    b->scratch_doubles = need;
+    CUDA_TRY(cudaMalloc(&b->d_scratch, sizeof(double) * 2 * need));
+    b->scratch_doubles = 2 * need;
   }
+  if (!b->side) {
+    CUDA_TRY(cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking));
+    CUDA_TRY(cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming));
+    CUDA_TRY(cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming));
+  }
+  const cudaStream_t ss[2] = {st, b->side};
   // ---- per job: zero outputs, density block maxima
   for (int j = 0; j < njobs; ++j) {
     eri_plan* p = plans[j];
@@ -1813,10 +1829,18 @@ eri_status eri_jk_batch(eri_batch* b, int njobs, eri_plan* const* plans, const d
   CUDA_TRY(cudaMemsetAsync(b->d_cursor, 0, sizeof(unsigned long long) * 2 * 256, st));
   CUDA_TRY(cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long) * 512, st));
   CUDA_TRY(cudaMemsetAsync(b->d_stats, 0, sizeof(unsigned long long) * 4 * 256, st));
-  // ---- per class: merged compaction over jobs, then one launch per precision
+  CUDA_TRY(cudaEventRecord(b->ev_fork, st));
+  CUDA_TRY(cudaStreamWaitEvent(b->side, b->ev_fork, 0));
+  // ---- per class (alternating streams): merged compaction over jobs, then one launch per
+  //      precision
   int li = 0;
   for (size_t ci = 0; ci < cls.size(); ++ci) {
     const BL& c = cls[ci];
+    const int sidx = (int)(ci & 1);
+    const cudaStream_t sl = ss[sidx];
+    unsigned long long* blist_l = b->d_blist + (size_t)sidx * cap;
+    unsigned* tiles_l = b->d_tiles + (size_t)sidx * tcap;
+    unsigned long long* small_l = b->d_small + 4 * sidx;
     unsigned long long* cursor = b->d_cursor + 2 * ci;
     for (int j = 0; j < njobs; ++j) {
       eri_plan* p = plans[j];
@@ -1834,31 +1858,33 @@ eri_status eri_jk_batch(eri_batch* b, int njobs, eri_plan* const* plans, const d
       a.nsh = p->nshell;
       a.tau = p->opts.screen_thresh;
       a.mixed_thr = p->opts.mixed_thresh;
-      CUDA_TRY(erik_launch_compact_batched(&a, b->d_blist, (unsigned long long)c.total, b->d_small, b->d_tiles,
-                                           cursor, b->d_small + 2, (unsigned long long)j,
-                                           p->opts.precision == ERI_MIXED ? 1 : 0, st));
+      CUDA_TRY(erik_launch_compact_batched(&a, blist_l, (unsigned long long)c.total, small_l, tiles_l, cursor,
+                                           small_l + 2, (unsigned long long)j,
+                                           p->opts.precision == ERI_MIXED ? 1 : 0, sl));
     }
     for (const LL& l : launches) {
       if (l.X != c.X || l.Y != c.Y) continue;
       KernelArgs a = base_args(p0, c.X, c.Y);
       a.mode = KMODE_JK;
       a.jobs = b->d_jobs;
-      a.blist = b->d_blist;
+      a.blist = blist_l;
       a.list_cap = (unsigned long long)c.total;
       a.from_back = l.fp32;
       a.tcount = cursor + l.fp32;
       a.X = c.X;
       a.Y = c.Y;
       a.counter = b->d_counter + li;
-      a.scratch = b->d_scratch;
+      a.scratch = b->d_scratch + (size_t)sidx * need;
       a.stats = b->d_stats + 2 * (256 * l.fp32 + c.X * ERI_NPAIRTYPE + c.Y);
       if (l.small)
-        CUDA_TRY(erik_launch_small(a.c.la, a.c.lb, a.c.lc, a.c.ld, l.fp32, &a, l.grid, st));
+        CUDA_TRY(erik_launch_small(a.c.la, a.c.lb, a.c.lc, a.c.ld, l.fp32, &a, l.grid, sl));
       else
-        CUDA_TRY(erik_launch_class(l.ts, l.fp32, &a, l.grid, l.smem, st));
+        CUDA_TRY(erik_launch_class(l.ts, l.fp32, &a, l.grid, l.smem, sl));
       ++li;
     }
   }
+  CUDA_TRY(cudaEventRecord(b->ev_join, b->side));
+  CUDA_TRY(cudaStreamWaitEvent(st, b->ev_join, 0));
   for (int j = 0; j < njobs; ++j) {
     if (flags[j] & 1) CUDA_TRY(erik_launch_symmetrize(J[j], nD[j], plans[j]->nbf, st));
     if (flags[j] & 2) CUDA_TRY(erik_launch_symmetrize(K[j], nD[j], plans[j]->nbf, st));
