@@ -34,7 +34,7 @@ typedef enum {
   ERI_ERR_OOM = 3,            /* device or host allocation failed; the plan is left unchanged */
   ERI_ERR_CUDA = 4,           /* a CUDA runtime call failed; message in eri_last_error() */
   ERI_ERR_NO_DEVICE = 5,      /* no CUDA device is visible */
-  ERI_ERR_TIMEOUT = 6,        /* a bounded wait gave up */
+  ERI_ERR_TIMEOUT = 6,        /* reserved for bounded device waits; no entry point waits on device flags */
   ERI_ERR_UNSUPPORTED_L = 7   /* angular momentum above g (l > 4); Sec. 3 stops at g */
 } eri_status;
 
