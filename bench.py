@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision measurement")
     ap.add_argument("--no-grad", action="store_true", help="skip the gradient measurement")
+    ap.add_argument("--no-serve", action="store_true", help="skip the served-workload measurement")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target wall time of the oracle sample")
     return ap.parse_args()
 
@@ -378,6 +379,22 @@ def run_ours(args):
                 "max_abs_sum_over_atoms": float(max(gJ.sum(0).abs().max(), gK.sum(0).abs().max()))}
         plan_g.close()
 
+    # ---- served workload (rank 0): continuous batching (mixed) against one-at-a-time FP64
+    served = None
+    if rank == 0 and not args.no_serve:
+        from workloads import config_served_requests
+        from paper_2407_09700_gb300.serve import Server, make_jobs, run_sequential
+        reqs = config_served_requests(seed=args.seed, nreq=32, mean_interarrival_s=0.02, natm_range=(5, 15))
+        Server().run(make_jobs(reqs[:1], natm_cap=5))        # warm kernels and allocator
+        sv = Server(hbm_budget=64 << 30, max_slots=32).run(make_jobs(reqs))
+        sq = run_sequential(make_jobs(reqs))
+        served = {"workload": "32 requests, exponential inter-arrival mean 20 ms (50 req/s), atoms log-uniform "
+                              "[5, 15], 30% RHF to 1e-8 Ha, 70% single J/K; heavy/light 3s2p1d/2s1p recipe",
+                  "served_mixed": {k: sv[k] for k in ("throughput_req_s", "p50_latency_s", "p99_latency_s",
+                                                      "makespan_s", "mean_batch")},
+                  "sequential_fp64": {k: sq[k] for k in ("throughput_req_s", "p50_latency_s", "p99_latency_s",
+                                                         "makespan_s")}}
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         b, qs, cores, desc = oracle_sample_rate(mol, args.cpu_seconds)
@@ -411,6 +428,7 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "mixed": mixed,
             "grad": grad,
+            "served": served,
             "kernel_shares": {k: round(v["ms"] / all_ms, 4) for k, v in sorted(per_kernel.items(), key=lambda kv: -kv[1]["ms"])[:8]},
         }
         print(json.dumps(line), flush=True)
