@@ -17,6 +17,17 @@
 static __device__ uchar4 c_cart[ERI_MAXCART];
 __device__ __forceinline__ uchar4 cart_of(int g) { return __ldg(c_cart + g); }
 
+// Copy the table to this translation unit's c_cart (x-descending order, l = 0..9).
+static inline cudaError_t upload_cart_table() {
+  uchar4 h[ERI_MAXCART];
+  int g = 0;
+  for (int l = 0; l <= ERI_CART_LMAX; ++l)
+    for (int lx = l; lx >= 0; --lx)
+      for (int ly = l - lx; ly >= 0; --ly)
+        h[g++] = make_uchar4((unsigned char)lx, (unsigned char)ly, (unsigned char)(l - lx - ly), (unsigned char)l);
+  return cudaMemcpyToSymbol(c_cart, h, sizeof(h));
+}
+
 __device__ __forceinline__ int cart_below(int l) { return l * (l + 1) * (l + 2) / 6; }
 __device__ __forceinline__ int cart_pos(int ly, int lz) { int r = ly + lz; return r * (r + 1) / 2 + lz; }
 __device__ __forceinline__ int cart_index(int lx, int ly, int lz) {

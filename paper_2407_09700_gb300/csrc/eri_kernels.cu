@@ -541,17 +541,7 @@ __global__ void fma_probe_kernel(Tp* out, int iters, Tp a, Tp b) {
 }
 
 // ------------------------------------------------------------------ host launchers
-extern "C" int erik_upload_cart_tables(void) {
-  uchar4 h[ERI_MAXCART];
-  int g = 0;
-  for (int l = 0; l <= ERI_CART_LMAX; ++l)
-    for (int lx = l; lx >= 0; --lx)
-      for (int ly = l - lx; ly >= 0; --ly) {
-        h[g] = make_uchar4((unsigned char)lx, (unsigned char)ly, (unsigned char)(l - lx - ly), (unsigned char)l);
-        ++g;
-      }
-  return (int)cudaMemcpyToSymbol(c_cart, h, sizeof(h));
-}
+extern "C" int erik_upload_cart_tables(void) { return (int)upload_cart_table(); }
 
 static const void* class_kernel_ptr(int ts, int fp32, int xy) {
   if (fp32) {

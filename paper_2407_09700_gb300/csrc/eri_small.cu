@@ -231,17 +231,7 @@ const void* small_ptr(int la, int lb, int lc, int ld, int fp32) {
 
 }  // namespace
 
-extern "C" int erik_upload_cart_tables_small(void) {
-  uchar4 h[ERI_MAXCART];
-  int g = 0;
-  for (int l = 0; l <= ERI_CART_LMAX; ++l)
-    for (int lx = l; lx >= 0; --lx)
-      for (int ly = l - lx; ly >= 0; --ly) {
-        h[g] = make_uchar4((unsigned char)lx, (unsigned char)ly, (unsigned char)(l - lx - ly), (unsigned char)l);
-        ++g;
-      }
-  return (int)cudaMemcpyToSymbol(c_cart, h, sizeof(h));
-}
+extern "C" int erik_upload_cart_tables_small(void) { return (int)upload_cart_table(); }
 
 // 1 if (la lb | lc ld) has a specialised kernel for this precision (fp32 = 1: FP32 path).
 extern "C" int erik_small_available(int la, int lb, int lc, int ld, int fp32) {
