@@ -41,6 +41,14 @@ def test_h2_sto3g_on_gpu():
     assert r.energy == pytest.approx(-1.1167, abs=1e-4)
 
 
+def test_heh_plus_sto3g_on_gpu():
+    """The textbook HeH+ / STO-3G example (Szabo & Ostlund, App. B: -2.860662 Hartree)."""
+    from test_onee_scf import heh_plus
+    r = RHF(heh_plus(), charge=1).kernel(conv_tol=1e-12, max_iter=100)
+    assert r.converged
+    assert r.energy == pytest.approx(-2.860662, abs=1e-5)
+
+
 def test_rhf_matches_oracle_rhf():
     m = _small(1)
     ref_E, ref_hist, _ = scf_ref.rhf(m, fixed_iters=12)

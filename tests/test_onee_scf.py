@@ -4,8 +4,10 @@
   against the oracle's quadrature (Gauss-Hermite per axis; Gaussian transform of 1/r).
 * The oracle's quadrature against closed forms for s functions.
 * The oracle's plain RHF against exact results: one basis function (E = 2 h + (11|11)
-  + E_nuc) and the textbook H2 / STO-3G energy at R = 1.4 bohr (Szabo & Ostlund,
-  "Modern Quantum Chemistry", Sec. 3.5: -1.117 Hartree), plus translation invariance.
+  + E_nuc), the textbook H2 / STO-3G energy at R = 1.4 bohr (Szabo & Ostlund,
+  "Modern Quantum Chemistry", Sec. 3.5: -1.117 Hartree) and the book's HeH+ / STO-3G
+  worked example at R = 1.4632 bohr (App. B: total energy -2.860662 Hartree, printed to
+  6 decimals from integrals of that program's precision), plus translation invariance.
 """
 
 import math
@@ -93,3 +95,19 @@ def test_rhf_translation_invariance():
     E1, _, _ = scf_ref.rhf(m)
     E2, _, _ = scf_ref.rhf(m.translated([2.0, -1.0, 0.5]))
     assert E1 == pytest.approx(E2, abs=1e-9)
+
+
+STO3G_1S = ([0.109818, 0.405771, 2.22766], [0.444635, 0.535328, 0.154329])   # zeta = 1 fit
+
+
+def heh_plus():
+    """HeH+ in STO-3G with zeta(He) = 2.0925, zeta(H) = 1.24 at R = 1.4632 bohr."""
+    a, d = (np.array(x) for x in STO3G_1S)
+    shells = [(0, 0, a * 2.0925 ** 2, d), (1, 0, a * 1.24 ** 2, d)]
+    return custom_molecule([[0, 0, 0], [0, 0, 1.4632]], shells, charges=[2.0, 1.0])
+
+
+def test_rhf_heh_plus_sto3g_textbook():
+    E, hist, conv = scf_ref.rhf(heh_plus(), charge=1, conv_tol=1e-12, max_iter=100)
+    assert conv
+    assert E == pytest.approx(-2.860662, abs=1e-5)
