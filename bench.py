@@ -131,25 +131,32 @@ class Clocks:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-        sm, smax, reasons, power = [], [], set(), []
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            parts = [p.strip() for p in ln.split(",")]
-            if len(parts) != len(self.FIELDS):
-                continue
-            try:
-                sm.append(float(parts[0]))
-                smax.append(float(parts[1]))
-                power.append(float(parts[6]))
-            except ValueError:
-                continue
-            for n, v in zip(names, parts[2:6]):
-                if v.lower().startswith("active"):
-                    reasons.add(n)
-        return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm),
-                "power_w_median": statistics.median(power) if power else None}
+        return summarize_clock_lines(self.lines)
+
+
+def summarize_clock_lines(lines):
+    """Median SM clock, maximum SM clock, the throttle reasons seen active and the median power
+    over nvidia-smi samples (clocks.sm, clocks.max.sm, hw_slowdown, hw_thermal_slowdown,
+    sw_thermal_slowdown, sw_power_cap, power.draw per line); malformed lines are skipped."""
+    sm, smax, reasons, power = [], [], set(), []
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for ln in lines:
+        parts = [p.strip() for p in ln.split(",")]
+        if len(parts) != len(Clocks.FIELDS):
+            continue
+        try:
+            sm.append(float(parts[0]))
+            smax.append(float(parts[1]))
+            power.append(float(parts[6]))
+        except ValueError:
+            continue
+        for n, v in zip(names, parts[2:6]):
+            if v.lower().startswith("active"):
+                reasons.add(n)
+    return {"sm_mhz": statistics.median(sm) if sm else None,
+            "sm_max_mhz": max(smax) if smax else None,
+            "reasons": sorted(reasons), "samples": len(sm),
+            "power_w_median": statistics.median(power) if power else None}
 
 
 def gpu_index(local):

@@ -122,3 +122,32 @@ def test_server_rejects_a_request_larger_than_the_budget():
     jobs = _jobs([("jk", 0, 0.0, 50)])
     with pytest.raises(RuntimeError, match="exceeds the HBM budget"):
         _server(hbm_budget=10, max_slots=2).run(jobs)
+
+
+# ---------------------------------------------------------------- bench helpers
+
+def test_clock_summary_flags_throttling_and_skips_bad_lines():
+    import bench
+    lines = ["2070, 2070, Not Active, Not Active, Not Active, Not Active, 290.5",
+             "2070, 2070, Not Active, Not Active, Not Active, Active, 1399.0",
+             "1980, 2070, Active, Not Active, Not Active, Not Active, 800.0",
+             "garbage line", "[N/A], 2070, Not Active, Not Active, Not Active, Not Active, 300"]
+    out = bench.summarize_clock_lines(lines)
+    assert out["samples"] == 3
+    assert out["sm_mhz"] == 2070.0 and out["sm_max_mhz"] == 2070.0
+    assert out["reasons"] == ["hw_slowdown", "sw_power_cap"]
+    assert out["power_w_median"] == 800.0
+    assert bench.summarize_clock_lines([])["sm_mhz"] is None
+
+
+def test_gpu_index_follows_visible_devices(monkeypatch):
+    import bench
+    monkeypatch.setenv("CUDA_VISIBLE_DEVICES", "3,5")
+    assert bench.gpu_index(0) == "3" and bench.gpu_index(1) == "5"
+    monkeypatch.delenv("CUDA_VISIBLE_DEVICES")
+    assert bench.gpu_index(2) == "2"
+
+
+def test_replica_throughput_counts_every_rank():
+    import bench
+    assert bench.replica_throughput(2, 4, 8.0) == pytest.approx(1.0)
