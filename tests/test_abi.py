@@ -102,3 +102,10 @@ def test_class_tables_self_check_with_overrides(lib):
     assert out.returncode == 0, out.stderr
     n, bad = map(int, out.stdout.split())
     assert n == 450 and bad == 0
+
+
+def test_binding_declares_every_header_symbol(lib):
+    """The ctypes binding gives every C-ABI entry point its signature (argument marshalling
+    only: no entry point is reached without argtypes)."""
+    missing = [n for n in pkg.header_symbols() if n not in E._SIGS]
+    assert not missing, missing
