@@ -47,7 +47,10 @@ class SCFResult:
 
 class RHF:
     def __init__(self, mol, charge: Optional[int] = None, precision: int = ERI_FP64, mixed_thresh: float = 1e-5,
-                 tau: Optional[float] = None, lindep: float = 1e-8, plan: Optional[Plan] = None, stream=None):
+                 tau: Optional[float] = None, lindep: float = 1e-8, plan: Optional[Plan] = None, stream=None,
+                 device: str = "cuda"):
+        """device: where the matrices live ("cuda"; the step-wise start / update interface also
+        runs on "cpu" with J and K supplied by the caller)."""
         import torch
         self.torch = torch
         self.mol = mol
@@ -60,7 +63,7 @@ class RHF:
         self.plan = plan if plan is not None else Plan(mol, tau=tau, precision=precision, mixed_thresh=mixed_thresh)
         self.stream = stream
         S, T, V = one_electron(mol)
-        dev = torch.device("cuda")
+        dev = torch.device(device)
         self.S = torch.from_numpy(S).to(dev)
         self.H = torch.from_numpy(T + V).to(dev)
         self.enuc = nuclear_repulsion(mol.coords, mol.charges)

@@ -151,3 +151,36 @@ def test_gpu_index_follows_visible_devices(monkeypatch):
 def test_replica_throughput_counts_every_rank():
     import bench
     assert bench.replica_throughput(2, 4, 8.0) == pytest.approx(1.0)
+
+
+# ---------------------------------------------------------------- RHF driver host logic
+
+def test_rhf_driver_steps_match_the_oracle_rhf_on_cpu():
+    """The driver's Fock build, energy, DIIS and density update (the step-wise interface the
+    server uses), run on CPU tensors with J and K from the oracle, against the oracle's own
+    plain RHF iteration by iteration (one-electron integrals from the library's host routine
+    on one side, quadrature on the other)."""
+    import oracle
+    from oracle import scf_ref
+    from paper_2407_09700_gb300.scf import RHF
+    from workloads import custom_molecule
+    import paper_2407_09700_gb300 as pkg
+    pkg.build()
+    rng = np.random.default_rng(1)
+    coords = np.array([[0.0, 0.0, 0.0], [1.9, 0.3, -0.2], [-0.7, 1.8, 0.4]])
+    shells = []
+    for a, ls in enumerate([(0, 0, 1, 2), (0, 1), (0, 1)]):
+        for l in ls:
+            K = int(rng.integers(1, 4))
+            shells.append((a, l, np.sort(rng.uniform(0.2, 4.0, K))[::-1], rng.uniform(0.2, 1.0, K)))
+    m = custom_molecule(coords, shells, charges=[6.0, 1.0, 1.0])
+    drv = RHF(m, plan=object(), device="cpu")
+    D = drv.start()
+    energies = []
+    for _ in range(10):
+        J, K, _ = oracle.jk(m, D=D.numpy()[None])
+        e, _ = drv.update(torch.from_numpy(J[0]), torch.from_numpy(K[0]), None)
+        energies.append(e)
+        D = drv.D
+    _, ref_hist, _ = scf_ref.rhf(m, fixed_iters=10)
+    np.testing.assert_allclose(energies, ref_hist, atol=1e-8, rtol=0)
