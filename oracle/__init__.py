@@ -22,4 +22,7 @@ from .oracle import (  # noqa: F401
     count_quartets,
     max_threads,
     OracleBasis,
+    OPS_PHASES,
+    quartet_ops,
+    class_ops,
 )

@@ -37,6 +37,16 @@
 #define ORC_LMAX 5   /* l <= 4 shells and their l+1 derivative companions */
 #define ORC_MMAX (4 * ORC_LMAX + 1)
 
+/* ------------------------------------------------------------------ operation counter
+ * Floating-point operations this oracle performs, by phase, on the calling thread: every
+ * add, subtract, multiply and divide of the source counts 1, each exp / sqrt / erf / pow
+ * call counts 1, negations and integer index arithmetic count 0.  The counts are added once per loop iteration from the statement counts
+ * written beside each loop (integer additions only, so the oracle's own speed is not
+ * affected).  oracle_class_ops reads them for one synthetic quartet of a class. */
+enum { OPS_PRIM = 0, OPS_BOYS, OPS_VRR, OPS_CONTRACT, OPS_HRR, OPS_DIGEST, OPS_N };
+static _Thread_local long long g_ops[OPS_N];
+#define COUNT_OPS(phase, n) (g_ops[phase] += (long long)(n))
+
 /* ------------------------------------------------------------------ Cartesian indexing */
 
 static int ncart(int l) { return (l + 1) * (l + 2) / 2; }
@@ -63,18 +73,25 @@ static void cart_lmn(int l, int pos, int v[3]) {
  *   F_{m+1} = ((2m+1) F_m - exp(-T)) / (2T), stable while T is large. */
 void oracle_boys(int mmax, double T, double* F) {
   double eT = exp(-T);
+  COUNT_OPS(OPS_BOYS, 1);                                   /* exp */
   if (T < 35.0) {
     double term = 1.0 / (2 * mmax + 1), sum = term;
+    COUNT_OPS(OPS_BOYS, 1);
     for (int k = 1; k < 100000; ++k) {
       term *= 2.0 * T / (2 * mmax + 2 * k + 1);
       sum += term;
+      COUNT_OPS(OPS_BOYS, 5);                               /* 2T, /, *=, +=, 1e-18 sum */
       if (term < 1e-18 * sum) break;
     }
     F[mmax] = eT * sum;
+    COUNT_OPS(OPS_BOYS, 1);
     for (int m = mmax; m > 0; --m) F[m - 1] = (2.0 * T * F[m] + eT) / (2 * m - 1);
+    COUNT_OPS(OPS_BOYS, 4 * mmax);
   } else {
     F[0] = 0.5 * sqrt(M_PI / T) * erf(sqrt(T));
+    COUNT_OPS(OPS_BOYS, 6);                                 /* pi/T, sqrt, sqrt, erf, two * */
     for (int m = 0; m < mmax; ++m) F[m + 1] = ((2 * m + 1) * F[m] - eT) / (2.0 * T);
+    COUNT_OPS(OPS_BOYS, 4 * mmax);
   }
 }
 
@@ -139,10 +156,15 @@ static void os_vrr(int Le, int Lf, double a, const double A[3], double b, const 
   double T = rho * PQ2;
   double theta = 2.0 * pow(M_PI, 2.5) / (zeta * eta * sqrt(s)) *
                  exp(-a * b / zeta * AB2) * exp(-c * d / eta * CD2);
+  /* zeta, eta, s, rho (2); per axis P, Q, W (4 each), PA WP QC WQ, AB2 CD2 PQ2 (two
+   * subtractions, a multiply and an add each); T; theta: pow, *, sqrt, two *, /, two exp with
+   * 4 operations each, two * */
+  COUNT_OPS(OPS_PRIM, 5 + 3 * (12 + 4 + 12) + 1 + 16);
   double F[ORC_MMAX + 1];
   oracle_boys(Lt, T, F);
 #define VV(e, f, m) V[((size_t)(e) * nf + (f)) * nm + (m)]
   for (int m = 0; m <= Lt; ++m) VV(0, 0, m) = theta * F[m];
+  COUNT_OPS(OPS_VRR, Lt + 1);
   /* bra: [e+1_i|0]^(m) = PA_i [e|0]^(m) + WP_i [e|0]^(m+1)
                           + e_i/(2 zeta) ([e-1_i|0]^(m) - rho/zeta [e-1_i|0]^(m+1)) */
   for (int le = 1; le <= Le; ++le)
@@ -159,6 +181,7 @@ static void os_vrr(int Le, int Lf, double a, const double A[3], double b, const 
         if (n > 0) v += n / (2.0 * zeta) * (VV(iemm, 0, m) - rho / zeta * VV(iemm, 0, m + 1));
         VV(ie, 0, m) = v;
       }
+      COUNT_OPS(OPS_VRR, (long long)(Lt - le + 1) * (n > 0 ? 3 + 7 : 3));
     }
   /* ket: [e|f+1_i]^(m) = QC_i [e|f]^(m) + WQ_i [e|f]^(m+1)
                           + f_i/(2 eta) ([e|f-1_i]^(m) - rho/eta [e|f-1_i]^(m+1))
@@ -184,6 +207,8 @@ static void os_vrr(int Le, int Lf, double a, const double A[3], double b, const 
             if (e[i] > 0) v += e[i] / (2.0 * s) * VV(iem, jfm, m + 1);
             VV(ie, jf, m) = v;
           }
+          if (Lt - le - lf >= 0)
+            COUNT_OPS(OPS_VRR, (long long)(Lt - le - lf + 1) * (3 + (n > 0 ? 7 : 0) + (e[i] > 0 ? 4 : 0)));
         }
     }
 #undef VV
@@ -220,6 +245,7 @@ static void hgp_hrr(int la, int lb, const double AB[3], int nv, const double* X,
         const double* x0 = cur + ((size_t)ia * nbm + pbm) * nv;
         double* y = nxt + ((size_t)ia * nb + pb) * nv;
         for (int v = 0; v < nv; ++v) y[v] = x1[v] + AB[i] * x0[v];
+        COUNT_OPS(OPS_HRR, 2LL * nv);
       }
     }
     (void)na_prev;
@@ -260,6 +286,7 @@ void oracle_shell_quartet(const obasis* bs, int I, int J, int K, int L, double* 
           for (int ie = 0; ie < ne; ++ie)
             for (int jf = 0; jf < nf; ++jf)
               E[(size_t)ie * nf + jf] += ca * V[((size_t)(ie + e0) * nf_all + (jf + f0)) * nm];
+          COUNT_OPS(OPS_CONTRACT, 3 + 2LL * ne * nf);
         }
   free(V);
   int na = ncart(la), nb = ncart(lb), nc = ncart(lc), nd = ncart(ld);
@@ -375,6 +402,7 @@ static void digest_block(const obasis* bs, const int* f0, int nbf, int nD, const
             Km[(size_t)x * nbf * nbf + (size_t)i * nbf + k] += v * Dx[(size_t)j * nbf + l];
           }
         }
+  COUNT_OPS(OPS_DIGEST, 4LL * nD * n[0] * n[1] * n[2] * n[3]);
 }
 
 int oracle_nbf(const obasis* bs) {
@@ -578,4 +606,47 @@ int oracle_max_threads(void) {
 #else
   return 1;
 #endif
+}
+
+/* ------------------------------------------------------------------ operation counts
+ * Operations of this oracle for one unique shell quartet (I J | K L) of bs whose eight
+ * ordered quartets are all distinct: the contracted quartet and the digestion of its orbit
+ * into J and K for nD densities.  out[OPS_N]: set-up, Boys, VRR, contraction, HRR,
+ * digestion.  Runs on the calling thread. */
+void oracle_quartet_ops(const obasis* bs, int I, int J, int K, int L, int nD, double* out) {
+  int sh[4] = {I, J, K, L}, n[4], nbf = oracle_nbf(bs);
+  size_t nabcd = 1;
+  for (int t = 0; t < 4; ++t) { n[t] = ncart(bs->l[sh[t]]); nabcd *= (size_t)n[t]; }
+  int* f0 = (int*)malloc(sizeof(int) * bs->nshell);
+  first_bf(bs, f0);
+  double* g = (double*)malloc(sizeof(double) * nabcd);
+  double* Dm = (double*)calloc((size_t)nD * nbf * nbf, sizeof(double));
+  double* Jm = (double*)calloc((size_t)nD * nbf * nbf, sizeof(double));
+  double* Km = (double*)calloc((size_t)nD * nbf * nbf, sizeof(double));
+  memset(g_ops, 0, sizeof(g_ops));
+  oracle_shell_quartet(bs, I, J, K, L, g);
+  for (int t = 0; t < 8; ++t) digest_block(bs, f0, nbf, nD, Dm, Jm, Km, sh, g, PERMS[t]);
+  for (int k = 0; k < OPS_N; ++k) out[k] = (double)g_ops[k];
+  free(f0); free(g); free(Dm); free(Jm); free(Km);
+}
+
+/* Operations per class (la lb | lc ld): ops = prim * sum(per_prim) + sum(per_quartet) for a
+ * quartet with prim primitive quartets.  per_prim[OPS_N] holds the set-up, Boys, VRR and
+ * contraction of one primitive quartet, per_quartet[OPS_N] the HRR and the digestion of nD
+ * densities (other entries 0).  Counted on one synthetic quartet with one primitive per shell
+ * (centres (0,0,0), (0,0,1.1), (0.9,0,0), (0.8,1.2,0.3) bohr, exponents 0.9, 0.6, 0.7, 0.5).
+ * Every phase but the Boys function is independent of the geometry and the exponents; the
+ * Boys series is counted at this geometry's T (about 0.3). */
+void oracle_class_ops(int la, int lb, int lc, int ld, int nD, double* per_prim, double* per_quartet) {
+  const double xyz[12] = {0.0, 0.0, 0.0, 0.0, 0.0, 1.1, 0.9, 0.0, 0.0, 0.8, 1.2, 0.3};
+  const int atom[4] = {0, 1, 2, 3}, l[4] = {la, lb, lc, ld}, nprim[4] = {1, 1, 1, 1}, off[4] = {0, 1, 2, 3};
+  const double exps[4] = {0.9, 0.6, 0.7, 0.5}, coefs[4] = {1.0, 1.0, 1.0, 1.0};
+  obasis bs = {4, xyz, 4, atom, l, nprim, off, exps, coefs};
+  double ops[OPS_N];
+  oracle_quartet_ops(&bs, 0, 1, 2, 3, nD, ops);
+  for (int k = 0; k < OPS_N; ++k) {
+    const int per_q = (k == OPS_HRR || k == OPS_DIGEST);
+    per_prim[k] = per_q ? 0.0 : ops[k];
+    per_quartet[k] = per_q ? ops[k] : 0.0;
+  }
 }

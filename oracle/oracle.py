@@ -68,6 +68,8 @@ def _get():
                                               ctypes.c_double, ctypes.c_int]
         lib.oracle_count_quartets.restype = ctypes.c_longlong
         lib.oracle_nbf.argtypes = [ctypes.POINTER(_OBasis)]
+        lib.oracle_quartet_ops.argtypes = [ctypes.POINTER(_OBasis)] + [ctypes.c_int] * 5 + [_dp]
+        lib.oracle_class_ops.argtypes = [ctypes.c_int] * 5 + [_dp, _dp]
         lib.oracle_max_threads.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -221,3 +223,25 @@ def count_quartets(mol, D=None, tau=None, screen: bool = True) -> int:
 
 def max_threads() -> int:
     return int(_get().oracle_max_threads())
+
+
+OPS_PHASES = ("setup", "boys", "vrr", "contract", "hrr", "digest")
+
+
+def quartet_ops(mol, i: int, j: int, k: int, l: int, nD: int = 1) -> dict:
+    """Floating-point operations the oracle performs for the unique quartet (ij|kl) (all eight
+    ordered quartets of its orbit taken as distinct) and its digestion of nD densities, by
+    phase (add, subtract, multiply, divide and each exp / sqrt / erf / pow count 1)."""
+    b = _basis(mol)
+    out = np.zeros(len(OPS_PHASES))
+    _get().oracle_quartet_ops(b.ptr(), int(i), int(j), int(k), int(l), int(nD), _d(out))
+    return dict(zip(OPS_PHASES, out.tolist()))
+
+
+def class_ops(la: int, lb: int, lc: int, ld: int, nD: int = 1):
+    """(per_prim, per_quartet) operation counts of the oracle for class (la lb|lc ld): a quartet
+    with P primitive quartets costs P * sum(per_prim) + sum(per_quartet) operations."""
+    pp = np.zeros(len(OPS_PHASES))
+    pq = np.zeros(len(OPS_PHASES))
+    _get().oracle_class_ops(int(la), int(lb), int(lc), int(ld), int(nD), _d(pp), _d(pq))
+    return dict(zip(OPS_PHASES, pp.tolist())), dict(zip(OPS_PHASES, pq.tolist()))
