@@ -31,9 +31,9 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "J/K builds/s & ERI quartets/s (FP64 vs mixed @1e-6); served p50/p99 latency"
-# split of the mixed mode: quartets with Schwarz x density bound <= 1e-5 run in FP32 (at 1e-4
-# the FP32 quartets' errors exceed the 1e-6 J/K target on this workload: max|dJ| 2.8e-6)
-MIXED_THRESH = 1e-5
+# split of the mixed mode: quartets whose transfer-aware Schwarz x density bound is <= 1e-4
+# run their recurrences in FP32
+MIXED_THRESH = 1e-4
 def workload_name(natm):
     return (f"medium J/K build: {natm} atoms, jittered 1.8 A lattice, 3s2p1d per atom, depths 1-6, "
             f"{15 * natm} Cartesian functions, 1 PSD density (60 columns), tau 1e-12, FP64")

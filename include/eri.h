@@ -60,9 +60,11 @@ typedef struct {
 typedef struct {
   double screen_thresh;      /* tau of Eqs. 6-9 (Sec. 3); shell pairs with Q <= tau are dropped */
   int precision;             /* ERI_FP64 (all FP64) or ERI_MIXED */
-  double mixed_thresh;       /* ERI_MIXED: a quartet whose bound Q_ij Q_kl max|D| (Eqs. 7-9) is <= this
-                                runs its recurrences, Eq. 1 products and contraction in FP32; Rys
-                                roots/weights, T, the transfer relations, digestion and J/K
+  double mixed_thresh;       /* ERI_MIXED: a quartet whose bound Qe_ij Qe_kl max|D| is <= this runs its
+                                recurrences, Eq. 1 products and contraction in FP32 (Qe: the
+                                transfer-aware Schwarz factor of eri_schwarz_transfer, >= the Q of
+                                Eq. 7, so every quartet above the Eqs. 7-9 bound stays FP64); Rys
+                                roots/weights, T, P - Q, the transfer relations, digestion and J/K
                                 accumulation stay FP64 */
   int max_nd;                /* largest nD an eri_jk call may pass (>= 1) */
 } eri_opts;
@@ -176,6 +178,19 @@ eri_status eri_shell_quartet(eri_plan* plan, int i, int j, int k, int l, double*
 
 /* Schwarz factors of Eq. 7 for every shell pair: Q[i*nshell+j] (HOST, symmetric). */
 eri_status eri_schwarz(const eri_plan* plan, double* Q);
+
+/*
+ * Transfer-aware factors of the mixed mode's precision split, for every shell pair:
+ * Qe[i*nshell+j] (HOST, symmetric) = sqrt(max_e [e0|e0]) (1 + max_x |A-B|_x)^lb, the
+ * Cauchy-Schwarz factor of the pair's contracted [e0| intermediates (|e| from la to la+lb,
+ * centre A of the shell with the larger l, before the transfer relations of Sec. 2) times
+ * the largest sum of absolute transfer coefficients, rounded up to FP32; Qe >= Q, equal to
+ * it (up to that rounding) when lb = 0.  The paper has no mixed precision; this is the
+ * library's reading of the Schwarz x density bound for the values that the FP32 stage
+ * computes.  A quartet of an ERI_MIXED plan runs in FP32 when it passes the screen and
+ * Qe_ij Qe_kl max|D| (six cross blocks) <= mixed_thresh.  Filled for every plan.
+ */
+eri_status eri_schwarz_transfer(const eri_plan* plan, double* Qe);
 
 /*
  * Rys roots and weights on the device, for testing the quadrature of Eq. 1:

@@ -302,14 +302,23 @@ __device__ __forceinline__ void resolve_task(const KernelArgs& a, long long task
   }
 }
 
-// Q_ij Q_kl max|D| over the six cross blocks (Eqs. 7-9)
-__device__ __forceinline__ double quartet_bound(const KernelArgs& a, const ShellPair* bra, const ShellPair* ket) {
+// Screening and precision of one unique quartet.  0: dropped, Q_ij Q_kl max|D| < tau with
+// max|D| over the six cross blocks (Eqs. 7-9); 1: FP64; 2: FP32 recurrences (mixed mode
+// only).  The mixed mode bounds what the FP32 stage produces, the contracted [e0|f0] before
+// the FP64 transfer relations: |[e0|f0]| <= sqrt([e0|e0] [f0|f0]) (Cauchy-Schwarz), and the
+// transfer relations multiply an [e0| error by at most (1 + max_x |A-B|_x)^lb, so the split
+// compares Qe_ij Qe_kl max|D| (>= the Eq. 7-9 bound; equal to it when lb = ld = 0) with
+// mixed_thr.
+__device__ __forceinline__ int quartet_category(const KernelArgs& a, const ShellPair* bra, const ShellPair* ket,
+                                                bool mixed) {
   const int P = bra->sh0, Qs = bra->sh1, Rr = ket->sh0, S = ket->sh1;
   const double* Dm = a.Dmax;
   const int n = a.nsh;
   const double dm = fmax(fmax(Dm[P * n + Qs], Dm[Rr * n + S]),
                          fmax(fmax(Dm[P * n + Rr], Dm[P * n + S]), fmax(Dm[Qs * n + Rr], Dm[Qs * n + S])));
-  return bra->Q * ket->Q * dm;
+  if (!(bra->Q * ket->Q * dm >= a.tau)) return 0;
+  if (!mixed) return 1;
+  return ((double)bra->Qe * (double)ket->Qe * dm > a.mixed_thr) ? 1 : 2;
 }
 
 // Per-primitive-quartet scalars in shared memory: NPD doubles (root lookup, FP64 always)
@@ -321,8 +330,6 @@ template <typename R> struct PairOf;
 template <> struct PairOf<double> { typedef PrimPair type; };
 template <> struct PairOf<float> { typedef PrimPairF type; };
 
-__device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
-__device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
 
 // Transfer relations on the contracted [e0|f0] in E0, then digestion into J~ / K~ (KMODE_JK),
 // the block (KMODE_BLOCK) or the diagonal maximum (KMODE_SCHWARZ).  Team-cooperative;
@@ -332,6 +339,15 @@ __device__ __forceinline__ void finish_quartet(const KernelArgs& a, const TaskCt
                                                R* bufA, R* bufB, int tl, bool active, const double* AB,
                                                const double* CD, const ShellPair* bra, const ShellPair* ket, int ib,
                                                int ik, long long task) {
+  if (a.mode == KMODE_SCHWARZ) {  // [e0|e0] of the diagonal quartet (ne = nf), before the transfer
+    double m = 0.0;
+    if (active)
+      for (int e = tl; e < c.ne; e += TS) m = fmax(m, fabs((double)E0[e * c.nf + e]));
+    if (TS > 1) {
+      for (int off = TS / 2; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
+    }
+    if (active && tl == 0) a.qout[a.ntask + task] = m;
+  }
   // ---- 2. transfer relations: bra on e (vector over f), then ket on f (vector over ab)
   const int nab = c.na * c.nb, ncd = c.nc * c.nd;
   const R* Y = hrr_team<R>(c.la, c.lb, AB, c.nf, E0, c.nf, 1, bufA, bufB, tl, TS, active);
@@ -426,7 +442,7 @@ __device__ __forceinline__ void finish_quartet(const KernelArgs& a, const TaskCt
         out[t] = (double)G[ab * sab + cd * scd];
       }
     }
-  } else {  // KMODE_SCHWARZ: bra and ket are the same pair; max_{a,b} |(ab|ab)|
+  } else {  // KMODE_SCHWARZ: bra and ket are the same pair; max_{a,b} |(ab|ab)|, max_e |[e0|e0]|
     double m = 0.0;
     if (active)
       for (int t = tl; t < nab; t += TS) m = fmax(m, fabs((double)G[t * sab + t * scd]));

@@ -19,14 +19,14 @@ struct PrimPair {
   double alpha;    // exponent of the primitive on A (the gradient kernels weight by 2 alpha, 2 beta)
 };
 
-// FP32 shadow of PrimPair for the FP32 path of the mixed mode.  40 bytes.
+// FP32 shadow of PrimPair for the FP32 path of the mixed mode (P - Q comes from the FP64
+// centres, so P itself is not shadowed).  32 bytes.
 struct PrimPairF {
   float zeta;
-  float P[3];
   float PA[3];
   float E;
   float hz;
-  float pad;
+  float pad[2];
 };
 
 // One shell pair in canonical orientation (l of sh0 >= l of sh1).  64 bytes.
@@ -36,7 +36,9 @@ struct ShellPair {
   int prim_off;    // first PrimPair
   int nprim;       // K_sh0 * K_sh1
   int ptype;       // l0 * (l0 + 1) / 2 + l1
-  int pair_id;     // index among all pairs i >= j (identifies the unordered pair)
+  float Qe;        // Cauchy-Schwarz factor of the pair's [e0| intermediates weighted by the
+                   // transfer coefficients, sqrt(max_e [e0|e0]) (1 + max_x |A-B|_x)^l1 >= Q: the
+                   // mixed mode's precision split uses Qe_ij Qe_kl max|D| (see quartet_category)
   double AB[3];    // A - B (A = centre of sh0)
   double Q;        // Cauchy-Schwarz factor of Eq. 7
 };
@@ -112,7 +114,8 @@ struct KernelArgs {
   const double* Dmax;    // [nsh][nsh]
   int nsh;
   double tau;
-  int prec_sel;          // 0: every kept quartet; 1: bound > mixed_thr only; 2: bound <= mixed_thr only
+  int prec_sel;          // 0: every kept quartet; 1: the FP64 quartets of the mixed split only; 2: its FP32
+                         // quartets only (quartet_category)
   double mixed_thr;
   // compacted task lists (KMODE_JK): when tlist is set, the tasks are tlist[0 .. *tcount) or,
   // with from_back, tlist[cap-1-t] for t < *tcount; they already passed the screen
@@ -135,7 +138,8 @@ struct KernelArgs {
   const int* tasklist;   // [2*ntask]
   double* blockout;      // KMODE_BLOCK: per task nabcd values, [cd][ab] layout as stored
   const long long* blockoff;
-  double* qout;          // KMODE_SCHWARZ: per task max_{a,b} |(ab|ab)|
+  double* qout;          // KMODE_SCHWARZ: per task max_{a,b} |(ab|ab)| at [task] and
+                         // max_e |[e0|e0]| (before the transfer relations) at [ntask + task]
   // scheduling, scratch, counters
   unsigned long long* counter;
   double* scratch;

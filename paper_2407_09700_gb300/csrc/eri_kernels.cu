@@ -37,9 +37,7 @@ __device__ __forceinline__ int task_category(const KernelArgs& a, long long task
   if (task >= a.ntask) return 0;
   int ib, ik;
   decode_task(a, task, ib, ik);
-  const double bound = quartet_bound(a, a.pairs + ib, a.pairs + ik);
-  if (!(bound >= a.tau)) return 0;
-  return (mixed && !(bound > a.mixed_thr)) ? 2 : 1;
+  return quartet_category(a, a.pairs + ib, a.pairs + ik, mixed != 0);
 }
 
 // Block-wide counts of categories 1 and 2 over one tile (256 threads x 4 tasks).
@@ -246,14 +244,11 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : ((sizeof(R) == 4 && !XY) ?
     const PP* prims_r = reinterpret_cast<const PP*>(sizeof(R) == 8 ? (const void*)tc.prims : (const void*)tc.primsf);
     const ShellPair* bra = tc.pairs + ib;
     const ShellPair* ket = tc.pairs + ik;
-    // ---- screening (Eqs. 7-9): Q_ij Q_kl max|D| over the six cross blocks >= tau;
-    //      in the mixed mode the same bound picks the precision (FP64 above mixed_thr).
-    //      Listed tasks were screened by compact_kernel.
+    // ---- screening (Eqs. 7-9) and, in the mixed mode, the precision split
+    //      (quartet_category).  Listed tasks were screened by the compaction.
     if (active && a.mode == KMODE_JK && !listed) {
-      const double bound = quartet_bound(a, bra, ket);
-      active = bound >= a.tau;
-      if (a.prec_sel == 1) active = active && bound > a.mixed_thr;
-      if (a.prec_sel == 2) active = active && !(bound > a.mixed_thr);
+      const int cat = quartet_category(a, bra, ket, a.prec_sel != 0);
+      active = cat != 0 && (a.prec_sel == 0 || cat == a.prec_sel);
     }
     const int npb = active ? bra->nprim : 0;
     const int npk = active ? ket->nprim : 0;
@@ -319,15 +314,10 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : ((sizeof(R) == 4 && !XY) ?
             const PP* x = (sizeof(R) == 8) ? reinterpret_cast<const PP*>(xd) : prims_r + ixp;
             const PP* y = (sizeof(R) == 8) ? reinterpret_cast<const PP*>(yd) : prims_r + iyp;
             const R zeta = x->zeta, eta = y->zeta;
-            R r, inv_s, P0, P1, P2;
-            if (sizeof(R) == 8) {
-              r = (R)rd;
-              P0 = (R)PQ0; P1 = (R)PQ1; P2 = (R)PQ2;
-            } else {
-              r = rsqrt_t(zeta + eta);
-              P0 = x->P[0] - y->P[0]; P1 = x->P[1] - y->P[1]; P2 = x->P[2] - y->P[2];
-            }
-            inv_s = r * r;
+            // P - Q and 1/sqrt(zeta + eta) from their FP64 values (P - Q formed in FP32 from
+            // rounded centres would carry an absolute error of ~|P| 6e-8 bohr)
+            const R r = (R)rd, P0 = (R)PQ0, P1 = (R)PQ1, P2 = (R)PQ2;
+            const R inv_s = r * r;
             const R rz = eta * inv_s, re = zeta * inv_s;
             const R hz = x->hz, he = y->hz;
             const int o = j * NPR;

@@ -15,6 +15,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <limits>
 #include <mutex>
 #include <new>
 #include <string>
@@ -631,6 +632,7 @@ struct eri_plan {
   int type_off[ERI_NPAIRTYPE] = {0}, type_cnt[ERI_NPAIRTYPE] = {0};
   int npairs_kept = 0;
   std::vector<double> Q;             // [nshell*nshell]
+  std::vector<double> Qe;            // [nshell*nshell] transfer-aware factors of the mixed split
   // device buffers
   ShellPair* d_pairs_all = nullptr;
   ShellPair* d_pairs = nullptr;
@@ -1093,7 +1095,7 @@ eri_status eri_plan_create(const eri_basis* basis, const eri_opts* opts, void* c
     sp.prim_off = (int)p->prims.size();
     sp.nprim = t.np;
     sp.ptype = t.t;
-    sp.pair_id = (int)k;
+    sp.Qe = 0.f;
     const double* A = &p->coords[3 * p->sh_atom[t.i]];
     const double* B = &p->coords[3 * p->sh_atom[t.j]];
     double AB2 = 0.0;
@@ -1152,13 +1154,10 @@ eri_status eri_plan_create(const eri_basis* basis, const eri_opts* opts, void* c
     const PrimPair& x = p->prims[k];
     PrimPairF& f = primsf[k];
     f.zeta = (float)x.zeta;
-    for (int c = 0; c < 3; ++c) {
-      f.P[c] = (float)x.P[c];
-      f.PA[c] = (float)x.PA[c];
-    }
+    for (int c = 0; c < 3; ++c) f.PA[c] = (float)x.PA[c];
     f.E = (float)x.E;
     f.hz = (float)x.hz;
-    f.pad = 0.f;
+    f.pad[0] = f.pad[1] = 0.f;
   }
   PLAN_TRY(cudaMemcpy(p->d_primsf, primsf.data(), sizeof(PrimPairF) * primsf.size(), cudaMemcpyHostToDevice));
   PLAN_TRY(cudaMemcpyAsync(p->d_sh_bf0, p->sh_bf0.data(), sizeof(int) * p->nshell, cudaMemcpyHostToDevice, st));
@@ -1166,23 +1165,35 @@ eri_status eri_plan_create(const eri_basis* basis, const eri_opts* opts, void* c
   PLAN_TRY(cudaMemcpyAsync(p->d_sh_atom, p->sh_atom.data(), sizeof(int) * p->nshell, cudaMemcpyHostToDevice, st));
   PLAN_TRY(cudaMemsetAsync(p->d_stats, 0, sizeof(unsigned long long) * 4 * 256, st));
 
-  // ---- Schwarz factors (Eq. 7) from the diagonal quartets (ij|ij), one class (X|X) at a time
+  // ---- Schwarz factors (Eq. 7) from the diagonal quartets (ij|ij), one class (X|X) at a time;
+  // the same launches give max_e [e0|e0] before the transfer relations, for the mixed mode's
+  // transfer-aware factor Qe = sqrt(max_e [e0|e0]) (1 + max_x |A-B|_x)^l1
   p->Q.assign((size_t)p->nshell * p->nshell, 0.0);
-  std::vector<double> qmax(npair, 0.0);
+  p->Qe.assign((size_t)p->nshell * p->nshell, 0.0);
+  std::vector<double> qmax(npair, 0.0), emax(npair, 0.0), qbuf;
   for (int X = 0; X < ERI_NPAIRTYPE; ++X) {
     const int n = p->type_cnt_all[X];
     if (n == 0) continue;
     std::vector<int> tasks(2 * n);
     for (int k = 0; k < n; ++k) tasks[2 * k] = tasks[2 * k + 1] = p->type_off_all[X] + k;
-    if ((s = run_explicit(p, X, X, KMODE_SCHWARZ, tasks, {}, n, st)) != ERI_OK) return cleanup(s);
-    PLAN_TRY(cudaMemcpyAsync(qmax.data() + p->type_off_all[X], p->d_out, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+    if ((s = run_explicit(p, X, X, KMODE_SCHWARZ, tasks, {}, 2 * (size_t)n, st)) != ERI_OK) return cleanup(s);
+    qbuf.resize(2 * (size_t)n);
+    PLAN_TRY(cudaMemcpyAsync(qbuf.data(), p->d_out, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost, st));
     PLAN_TRY(cudaStreamSynchronize(st));
+    std::copy(qbuf.begin(), qbuf.begin() + n, qmax.begin() + p->type_off_all[X]);
+    std::copy(qbuf.begin() + n, qbuf.end(), emax.begin() + p->type_off_all[X]);
   }
   for (size_t k = 0; k < npair; ++k) {
     ShellPair& sp = p->pairs_all[k];
     sp.Q = std::sqrt(qmax[k]);
+    const double ab = std::max(std::fabs(sp.AB[0]), std::max(std::fabs(sp.AB[1]), std::fabs(sp.AB[2])));
+    const double qe = std::sqrt(emax[k]) * std::pow(1.0 + ab, p->sh_l[sp.sh1]);
+    // rounded up so that the FP32 factor never falls below the FP64 one
+    sp.Qe = std::nextafter((float)std::max(qe, sp.Q), std::numeric_limits<float>::infinity());
     p->Q[(size_t)sp.sh0 * p->nshell + sp.sh1] = sp.Q;
     p->Q[(size_t)sp.sh1 * p->nshell + sp.sh0] = sp.Q;
+    p->Qe[(size_t)sp.sh0 * p->nshell + sp.sh1] = (double)sp.Qe;
+    p->Qe[(size_t)sp.sh1 * p->nshell + sp.sh0] = (double)sp.Qe;
   }
   PLAN_TRY(cudaMemcpyAsync(p->d_pairs_all, p->pairs_all.data(), sizeof(ShellPair) * npair, cudaMemcpyHostToDevice, st));
 
@@ -1410,6 +1421,13 @@ eri_status eri_schwarz(const eri_plan* p, double* Q) {
   g_err.clear();
   if (!p || !Q) return fail(ERI_ERR_ARG, "plan or Q is NULL");
   memcpy(Q, p->Q.data(), sizeof(double) * p->Q.size());
+  return ERI_OK;
+}
+
+eri_status eri_schwarz_transfer(const eri_plan* p, double* Qe) {
+  g_err.clear();
+  if (!p || !Qe) return fail(ERI_ERR_ARG, "plan or Qe is NULL");
+  memcpy(Qe, p->Qe.data(), sizeof(double) * p->Qe.size());
   return ERI_OK;
 }
 

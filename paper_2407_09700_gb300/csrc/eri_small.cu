@@ -79,10 +79,8 @@ __global__ void __launch_bounds__(TPB, (Small<LA, LB, LC, LD>::NOUT > 32 ? 2 : 3
     const ShellPair* bra = tc.pairs + ib;
     const ShellPair* ket = tc.pairs + ik;
     if (active && !listed) {
-      const double bound = quartet_bound(a, bra, ket);
-      active = bound >= a.tau;
-      if (a.prec_sel == 1) active = active && bound > a.mixed_thr;
-      if (a.prec_sel == 2) active = active && !(bound > a.mixed_thr);
+      const int cat = quartet_category(a, bra, ket, a.prec_sel != 0);
+      active = cat != 0 && (a.prec_sel == 0 || cat == a.prec_sel);
     }
     const int npb = active ? bra->nprim : 0;
     const int npk = active ? ket->nprim : 0;
@@ -117,14 +115,9 @@ __global__ void __launch_bounds__(TPB, (Small<LA, LB, LC, LD>::NOUT > 32 ? 2 : 3
         const PP* x = (sizeof(R) == 8) ? reinterpret_cast<const PP*>(xd) : prims_r + ixp;
         const PP* y = (sizeof(R) == 8) ? reinterpret_cast<const PP*>(yd) : prims_r + iyp;
         const R zeta = x->zeta, eta = y->zeta;
-        R r, P0, P1, P2;
-        if (sizeof(R) == 8) {
-          r = (R)rd;
-          P0 = (R)PQ0; P1 = (R)PQ1; P2 = (R)PQ2;
-        } else {
-          r = rsqrt_t(zeta + eta);
-          P0 = x->P[0] - y->P[0]; P1 = x->P[1] - y->P[1]; P2 = x->P[2] - y->P[2];
-        }
+        // P - Q and 1/sqrt(zeta + eta) from their FP64 values: P - Q formed in FP32 from rounded
+        // centres would carry an absolute error of ~|P| 6e-8 bohr
+        const R r = (R)rd, P0 = (R)PQ0, P1 = (R)PQ1, P2 = (R)PQ2;
         const R inv_s = r * r;
         const R rz = eta * inv_s, re = zeta * inv_s;
         const R hs = R(0.5) * inv_s;

@@ -76,6 +76,7 @@ _SIGS = {
                                       ctypes.POINTER(ctypes.c_longlong)]),
     "eri_shell_quartet": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int] * 4 + [_dp]),
     "eri_schwarz": (ctypes.c_int, [ctypes.c_void_p, _dp]),
+    "eri_schwarz_transfer": (ctypes.c_int, [ctypes.c_void_p, _dp]),
     "eri_rys_roots": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp]),
     "eri_flop_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(eri_stats)]),
     "eri_probe_fma_peak": (ctypes.c_int, [_dp, _dp]),
@@ -143,7 +144,7 @@ def _stream_handle(stream):
 class Plan:
     """An eri_plan built from a molecule-like object (coords, shell_* arrays, exps, coefs)."""
 
-    def __init__(self, mol, tau=None, precision=ERI_FP64, mixed_thresh=1e-5, max_nd=8, normalise=True,
+    def __init__(self, mol, tau=None, precision=ERI_FP64, mixed_thresh=1e-4, max_nd=8, normalise=True,
                  stream=None):
         lib = load_library()
         self._arrs = dict(
@@ -245,6 +246,11 @@ class Plan:
         Q = np.zeros((self.nshell, self.nshell))
         _check(load_library().eri_schwarz(self._h, _d(Q)))
         return Q
+
+    def schwarz_transfer(self):
+        Qe = np.zeros((self.nshell, self.nshell))
+        _check(load_library().eri_schwarz_transfer(self._h, _d(Qe)))
+        return Qe
 
     def set_profiling(self, on=True):
         _check(load_library().eri_set_profiling(self._h, 1 if on else 0))

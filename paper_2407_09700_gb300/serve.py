@@ -68,7 +68,7 @@ def _percentile(x, q):
 
 
 class Server:
-    def __init__(self, precision: int = ERI_MIXED, mixed_thresh: float = 1e-5, hbm_budget: int = 8 << 30,
+    def __init__(self, precision: int = ERI_MIXED, mixed_thresh: float = 1e-4, hbm_budget: int = 8 << 30,
                  max_slots: int = 32, scf_conv: float = 1e-8, scf_max_iter: int = 100, batch=None, sync=None):
         """batch: the batched J/K engine (an eri_batch by default); sync: waits for the device
         (torch.cuda.synchronize by default).  Both are replaceable so that the admission and

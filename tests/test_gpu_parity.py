@@ -160,9 +160,10 @@ def test_jk_high_l_reduced():
 
 # ---------------------------------------------------------------- mixed precision (FP32 recurrences)
 
-def _expected_split(m, Q, tau, thr):
-    """Unique shell quartets passing the screen, split by the mixed-precision bound
-    Q_ij * Q_kl * max|D| (six cross blocks), evaluated in the kernel's order of operations."""
+def _expected_split(m, Q, Qe, tau, thr):
+    """Unique shell quartets passing the screen Q_ij * Q_kl * max|D| >= tau (six cross blocks),
+    split by the mixed mode's bound Qe_ij * Qe_kl * max|D| > thr (FP64) or <= thr (FP32),
+    evaluated in the kernel's order of operations."""
     f0 = m.shell_first_bf()
     ns = m.nshell
     nf = [(int(l) + 1) * (int(l) + 2) // 2 for l in m.shell_l]
@@ -177,28 +178,69 @@ def _expected_split(m, Q, tau, thr):
         for b in range(a + 1):
             R, S = pairs[b]
             dm = max(max(Dmax[P, Qs], Dmax[R, S]), max(max(Dmax[P, R], Dmax[P, S]), max(Dmax[Qs, R], Dmax[Qs, S])))
-            bound = Q[P, Qs] * Q[R, S] * dm
-            if bound >= tau:
-                if bound > thr:
+            if Q[P, Qs] * Q[R, S] * dm >= tau:
+                if Qe[P, Qs] * Qe[R, S] * dm > thr:
                     n64 += 1
                 else:
                     n32 += 1
     return n64, n32
 
 
-@pytest.mark.parametrize("make", [lambda: config_medium(seed=5, natm=4), lambda: _mixed_molecule(seed=3, spread=4.0),
-                                  lambda: config_high_l(seed=6, natm=2, nocc=20)])
-def test_jk_mixed_precision_within_1e6(make):
+MIXED_THRESH = 1e-4      # the split of the mixed mode: FP64 above a bound of 1e-4
+
+
+@pytest.mark.parametrize("make,some_fp32", [(lambda: config_medium(seed=5, natm=4), True),
+                                             (lambda: _mixed_molecule(seed=3, spread=4.0), True),
+                                             (lambda: config_high_l(seed=6, natm=2, nocc=20), False)])
+def test_jk_mixed_precision_within_1e6(make, some_fp32):
     m = make()
-    plan = pkg.Plan(m, precision=pkg.ERI_MIXED, mixed_thresh=1e-5)
+    plan = pkg.Plan(m, precision=pkg.ERI_MIXED, mixed_thresh=MIXED_THRESH)
     J, K = _jk_gpu(plan, m.D)
     Jr, Kr, n = oracle.jk(m)
     st = plan.stats()
-    n64, n32 = _expected_split(m, plan.schwarz(), m.tau, 1e-5)
+    n64, n32 = _expected_split(m, plan.schwarz(), plan.schwarz_transfer(), m.tau, MIXED_THRESH)
     assert st["quartets_computed"] == n64 + n32
     assert st["quartets_fp32"] == n32
+    assert n32 > 0 or not some_fp32
     dj, dk = np.abs(J - Jr).max(), np.abs(K - Kr).max()
     assert dj <= 1e-6 and dk <= 1e-6, (dj, dk)
+
+
+def test_transfer_aware_factor_against_oracle():
+    """Qe of every shell pair: at least Q; equal to Q (FP32 rounding up) when the pair's second
+    shell is s; and sqrt(max_e [e0|e0]) (1 + max_x |A-B|_x)^lb with [e0|e0] from the oracle
+    (a shell of l = |e| with the first shell's exponents and normalised coefficients on A and an
+    s shell with the second shell's on B) for every pair with la + lb <= 4."""
+    m = _mixed_molecule(seed=9, natm=3, lmax=2, kmax=3, spread=2.5)
+    plan = pkg.Plan(m, tau=0.0)
+    Q, Qe = plan.schwarz(), plan.schwarz_transfer()
+    c = oracle.normalise(m)
+    checked = 0
+    for i in range(m.nshell):
+        for j in range(i + 1):
+            a, b = i, j
+            if m.shell_l[b] > m.shell_l[a]:
+                a, b = b, a
+            la, lb = int(m.shell_l[a]), int(m.shell_l[b])
+            assert Qe[i, j] >= Q[i, j] * (1 - 1e-12)
+            if lb == 0:
+                assert Qe[i, j] <= Q[i, j] * (1 + 3e-7) + 1e-300
+            if la + lb > 4:
+                continue
+            sa = slice(m.shell_off[a], m.shell_off[a] + m.shell_nprim[a])
+            sb = slice(m.shell_off[b], m.shell_off[b] + m.shell_nprim[b])
+            A, B = m.coords[m.shell_atom[a]], m.coords[m.shell_atom[b]]
+            emax = 0.0
+            for L in range(la, la + lb + 1):
+                mb = custom_molecule(np.stack([A, B]), [(0, L, m.exps[sa], c[sa]), (1, 0, m.exps[sb], c[sb])])
+                blk = oracle.shell_quartet(oracle.OracleBasis(mb, coefs=mb.coefs), 0, 1, 0, 1)
+                n = blk.shape[0]
+                emax = max(emax, max(abs(blk[e, 0, e, 0]) for e in range(n)))
+            h = (1.0 + np.abs(A - B).max()) ** lb
+            ref = np.sqrt(emax) * h
+            assert abs(Qe[i, j] - ref) <= 3e-7 * ref, (i, j, Qe[i, j], ref)
+            checked += 1
+    assert checked > 10
 
 
 def test_mixed_threshold_extremes():
@@ -351,13 +393,13 @@ def _check_blocks(m, pairs, Jl, Kl, J, K, tol):
 
 
 @pytest.mark.parametrize("name,precision,tol", [("medium", pkg.ERI_FP64, 1e-10), ("medium", pkg.ERI_MIXED, 1e-6),
-                                                ("high_l", pkg.ERI_FP64, 1e-10)])
+                                                ("high_l", pkg.ERI_FP64, 1e-10), ("high_l", pkg.ERI_MIXED, 1e-6)])
 def test_jk_full_size_sampled_blocks(name, precision, tol):
     """The 30-atom medium build the benchmark times (and the 12-atom s..g build) through
     eri_jk in its launch configuration, against oracle J / K blocks on sampled shell pairs
-    covering every pair of angular momenta; the mixed build at the bench's split 1e-5."""
+    covering every pair of angular momenta; the mixed builds at the split 1e-4."""
     m, pairs, Jl, Kl = _full_case(name)
-    plan = pkg.Plan(m, precision=precision, mixed_thresh=1e-5)
+    plan = pkg.Plan(m, precision=precision, mixed_thresh=MIXED_THRESH)
     J, K = _jk_gpu(plan, m.D)
     _check_blocks(m, pairs, Jl, Kl, J, K, tol)
     st = plan.stats()
