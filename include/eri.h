@@ -34,7 +34,7 @@ typedef enum {
   ERI_ERR_OOM = 3,            /* device or host allocation failed; the plan is left unchanged */
   ERI_ERR_CUDA = 4,           /* a CUDA runtime call failed; message in eri_last_error() */
   ERI_ERR_NO_DEVICE = 5,      /* no CUDA device is visible */
-  ERI_ERR_TIMEOUT = 6,        /* reserved for bounded device waits; no entry point waits on device flags */
+  ERI_ERR_TIMEOUT = 6,        /* a bounded device wait gave up (eri_flop_stats reports it) */
   ERI_ERR_UNSUPPORTED_L = 7   /* angular momentum above g (l > 4); Sec. 3 stops at g */
 } eri_status;
 
@@ -67,6 +67,14 @@ typedef struct {
                                 roots/weights, T, P - Q, the transfer relations, digestion and J/K
                                 accumulation stay FP64 */
   int max_nd;                /* largest nD an eri_jk call may pass (>= 1) */
+  int mixed_min_tasks;       /* ERI_MIXED: a class gets its FP32 launch only when its task space (unique
+                                quartets of its pair types before screening) has at least this many
+                                quartets; smaller classes run every quartet in FP64, where a second
+                                launch would cost more than the FP32 arithmetic saves.  0: every class. */
+  int check_symmetric;       /* 1: eri_jk and eri_jk_host first verify that every D is symmetric
+                                (max|D_ij - D_ji| <= 1e-12 max|D|, see eri_check_density) and return
+                                ERI_ERR_ARG otherwise; eri_jk then synchronises its stream.  0: not
+                                checked.  The 8-fold symmetry of Sec. 3 needs a symmetric D. */
 } eri_opts;
 
 /* Counters of the last eri_jk call on the plan (filled after that call's stream completes). */
@@ -80,16 +88,30 @@ typedef struct {
   int npairs_kept;                /* shell pairs with Q > tau */
   int nclasses_launched;          /* class kernel launches (two per class in ERI_MIXED) */
   double model_flops_fp32;        /* the FP32 part of model_flops (ERI_MIXED) */
+  int device_status;              /* 0, or 1 once a kernel of the plan gave up a bounded wait (the
+                                     bulk-copy staging of the tuning override); then
+                                     eri_flop_stats returns ERI_ERR_TIMEOUT and results since
+                                     are incomplete */
 } eri_stats;
+
+/*
+ * Symmetry check of nD densities [nD][nbf][nbf] in HOST memory: ERI_OK when max over the
+ * densities of |D_ij - D_ji| <= 1e-12 max|D| and every element is finite, ERI_ERR_ARG
+ * otherwise (message in eri_last_error).  Needs no GPU.  The J/K build's digestion
+ * (Alg. 2's six updates with the weights of the 8-fold symmetry, Sec. 3) is correct only for
+ * symmetric D.
+ */
+eri_status eri_check_density(const double* D, int nD, int nbf);
 
 /*
  * Create a plan: validates and normalises the basis, forms every shell pair
  * (i >= j) with its primitive-pair data (Gaussian product theorem, Eq. 2),
  * computes the Cauchy-Schwarz factors Q_ij = max |(ab|ab)|^(1/2) of Eq. 7 on
  * the GPU, keeps pairs with Q > tau and groups them by angular-momentum class
- * (Alg. 1 of Sec. 3).  Synchronous.  The plan owns all its device memory.
- * cuda_stream: a cudaStream_t or NULL for the default stream.
- * Errors: ERI_ERR_ARG (null pointers, tau < 0, max_nd < 1), ERI_ERR_BASIS,
+ * (Alg. 1 of Sec. 3).  Synchronous.  The plan owns all its device memory, including
+ * eri_jk's scratch, task lists and tile counts, which are sized here from the plan so that
+ * eri_jk itself allocates nothing.  cuda_stream: a cudaStream_t or NULL for the default stream.
+ * Errors: ERI_ERR_ARG (null pointers, tau < 0, max_nd < 1, check_symmetric not 0 / 1), ERI_ERR_BASIS,
  * ERI_ERR_UNSUPPORTED_L, ERI_ERR_NO_DEVICE, ERI_ERR_OOM, ERI_ERR_CUDA.
  */
 eri_status eri_plan_create(const eri_basis* basis, const eri_opts* opts, void* cuda_stream,
@@ -108,22 +130,25 @@ int eri_plan_nbf(const eri_plan* plan);
  * and the screening of Eqs. 7-9: a unique shell quartet is evaluated when
  * Q_ij * Q_kl * max|D| over its six cross blocks >= tau.
  * D, J, K: DEVICE pointers, contiguous [nD][nbf][nbf] FP64, 1 <= nD <= max_nd.
- * D must be symmetric (not checked).  J and K are overwritten, never
- * accumulated.  flags: ERI_WANT_J | ERI_WANT_K (an unwanted output may be
- * NULL and is not touched).  Asynchronous on cuda_stream; the plan's scratch is
- * reused by every call, so calls on one plan must not overlap on the GPU.
+ * D must be symmetric (checked only when the plan's check_symmetric is 1: ERI_ERR_ARG).
+ * J and K are overwritten, never accumulated.  flags: ERI_WANT_J | ERI_WANT_K (an unwanted
+ * output may be NULL and is not touched).  Asynchronous on cuda_stream (unless
+ * check_symmetric); allocates no device memory (the plan's buffers were sized at
+ * creation); the plan's scratch is reused by every call, so calls on one plan must not
+ * overlap on the GPU.
  */
 eri_status eri_jk(eri_plan* plan, const double* D, int nD, double* J, double* K, int flags,
                   void* cuda_stream);
 
 /*
  * eri_jk for callers that cannot allocate device memory during the call.  The
- * paper has no counterpart; this is a library convenience.  eri_jk may grow
- * the plan's scratch with cudaMalloc (after synchronising the device) the
- * first time a larger class is launched; code inside CUDA stream capture, in a
- * host callback, or under an allocator that owns all device memory cannot
- * allow that.  This call allocates nothing and calls no cudaMalloc / cudaFree
- * or allocating library routine: the class kernels' scratch is a file-scope
+ * paper has no counterpart; this is a library convenience.  A plan owns scratch
+ * sized for eri_jk, but eri_jk_grad and eri_shell_quartet may regrow it with
+ * cudaMalloc / cudaFree (after synchronising the device); code running under an
+ * allocator or a memory budget that owns all device memory, or in a host
+ * callback, must not let a library call those at all.  This call allocates
+ * nothing and calls no cudaMalloc / cudaFree or allocating library routine,
+ * and it leaves the plan's own scratch untouched: the class kernels' scratch is a file-scope
  * static device array of 32 MiB (ERI_NOALLOC_SCRATCH_BYTES) that every GPU
  * loading the library holds until the process exits.  Arguments, layout and
  * results are those of eri_jk (D, J, K device pointers; J and K overwritten).
@@ -134,7 +159,10 @@ eri_status eri_jk(eri_plan* plan, const double* D, int nD, double* J, double* K,
  * that overlap on the GPU, on any plan, race on it.  A class launch uses as
  * many blocks as the array can hold; a class whose single block needs more
  * scratch than the array is rejected with ERI_ERR_ARG before any launch.
- * The plan must belong to the current device (ERI_ERR_ARG otherwise).
+ * The plan must belong to the current device (ERI_ERR_ARG otherwise).  The
+ * cached address does not survive cudaDeviceReset (or the end of the primary
+ * context): after one, the process must not call this entry point on that device.
+ * A call leaves no per-launch records (eri_launch_records then reports none).
  */
 eri_status eri_jk_noalloc(eri_plan* plan, const double* D, int nD, double* J, double* K, int flags,
                           void* cuda_stream);

@@ -82,6 +82,8 @@ struct ClassDesc {
   const uint32_t* xytab;       // [products] ix | iy << 8
   const uint32_t* passinfo;    // [xy_npass][2] first product, products in the pass
   int ncomb;                   // distinct products of the class
+  int stage;                   // 1: stage each team's bra / ket PrimPair records into shared memory
+                               // by bulk copy (tuning override; kernels compiled for the class only)
   // offsets of the tables in the class's block of the device table (host bookkeeping)
   int dst_off, gmask_off, xy_outidx_off, xy_dst_off, xytab_off, pass_off;
 };
@@ -144,6 +146,7 @@ struct KernelArgs {
   unsigned long long* counter;
   double* scratch;
   unsigned long long* stats;   // [0] quartets computed, [1] primitive quartets
+  unsigned* err;               // set to 1 when a bounded device wait gave up (staged kernels)
   // Rys table for this class's root count
   const double* rys_coef;      // block of this N
   const double* rys_au;
@@ -198,6 +201,11 @@ extern "C" {
 int erik_upload_cart_tables(void);
 int erik_blocks_per_sm(int ts, int fp32, int xy, int smem_bytes, int* out);
 int erik_launch_class(int ts, int fp32, const struct KernelArgs* a, int grid, int smem_bytes, void* stream);
+// FP64 class kernels compiled for one class (eri_class_spec.cu): launches and returns 1 (launch
+// status in *rc) when one matches the class, team size and assembly path, else returns 0
+int erik_launch_class_spec(int ts, int xy, const struct KernelArgs* a, int grid, int smem_bytes, void* stream, int* rc);
+int erik_class_spec_prepare(void);
+int erik_upload_cart_tables_spec(void);
 int erik_launch_compact(const struct KernelArgs* a, unsigned* tlist, unsigned long long cap,
                         unsigned long long* counts, unsigned* tiles, int mixed, void* stream);
 int erik_launch_compact_batched(const struct KernelArgs* a, unsigned long long* blist, unsigned long long cap,
@@ -206,6 +214,7 @@ int erik_launch_compact_batched(const struct KernelArgs* a, unsigned long long* 
 int erik_launch_dmax(const double* D, int nD, int nbf, int nsh, const int* sh_bf0, const int* sh_n,
                      double* Dmax, void* stream);
 int erik_launch_symmetrize(double* M, int nD, int nbf, void* stream);
+int erik_launch_symcheck(const double* D, int nD, int nbf, unsigned long long* out, void* stream);
 int erik_launch_rys(int N, int n, const double* T, double* u, double* w, const double* coef,
                     const double* au, const double* aw, int tcut, void* stream);
 int erik_probe_fma(double* fp64_tflops, double* fp32_tflops);

@@ -24,7 +24,7 @@
 
 #include "eri_internal.h"
 
-#include "eri_device.cuh"
+#include "eri_class_kernel.cuh"
 
 // Stable compaction of a class's task space into the FP64 list (front of tlist, ascending
 // task order) and, in the mixed mode, the FP32 list (back of tlist, read back-to-front in
@@ -32,7 +32,6 @@
 // ordered writes.  Keeping the order keeps neighbouring tasks on the same bra pair and on
 // ket pairs of equal contraction depth, so a warp's primitive loops stay uniform.
 #define CTILE 1024
-#define XQ 12      // product indices a lane keeps in registers (products path)
 __device__ __forceinline__ int task_category(const KernelArgs& a, long long task, int mixed) {
   if (task >= a.ntask) return 0;
   int ib, ik;
@@ -171,308 +170,6 @@ __global__ void compact_write_batched_kernel(const KernelArgs a, int mixed, cons
   }
 }
 
-// ------------------------------------------------------------------ the class kernel
-// R = double: the FP64 path.  R = float: the FP32 path of the mixed mode (Sec. 2's
-// recurrences, Eq. 1's products and the Eq. 5 contraction in FP32; T and the Rys roots /
-// weights in FP64, rounded at the recurrence input; the transfer relations, digestion and
-// the J / K accumulation in FP64).
-template <int TS, typename R, bool XY>
-__global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : ((sizeof(R) == 4 && !XY) ? 3 : 2))) eri_class_kernel(const KernelArgs a) {
-  extern __shared__ double smem[];
-  typedef typename PairOf<R>::type PP;
-  constexpr int TEAMS_PER_WARP = 32 / TS;
-  const int lane = threadIdx.x & 31;
-  const int tl = lane % TS;                          // lane within team
-  const int team_in_block = threadIdx.x / TS;
-  const long long gteam = (long long)blockIdx.x * (TPB / TS) + team_in_block;
-  const ClassDesc& c = a.c;
-  const int N = c.nroots, nI = c.nI, Le = c.Le, Lf = c.Lf;
-  const int bp = XY ? c.bp_xy : c.bp;
-  const int npass = XY ? c.xy_npass : c.npass;
-  const int nslot = XY ? c.nout : c.nslot;
-  const uint32_t* outidx = XY ? c.xy_outidx : c.outidx;
-  const uint32_t* dsttab = XY ? c.xy_dst : c.dst;
-
-  // team region: [bp][NPD] doubles, then [bp][NPR] R, then [bp][3][N][nI] R
-  Smem<double> sd;
-  Smem<R> sr;
-  if (TS == 1) {
-    sd.base = smem + threadIdx.x;
-    sd.es = TPB;
-    sr.base = reinterpret_cast<R*>(smem + (size_t)TPB * bp * NPD) + threadIdx.x;
-    sr.es = TPB;
-  } else {
-    sd.base = smem + (size_t)team_in_block * (XY ? c.team_doubles_xy : (sizeof(R) == 8 ? c.team_doubles : c.team_doubles_f32));
-    sd.es = 1;
-    sr.base = reinterpret_cast<R*>(sd.base + bp * NPD);
-    sr.es = 1;
-  }
-  const int S_2D = bp * NPR;                         // R offset of the 2D tables
-  R* xyb = XY ? &sr[S_2D + bp * 3 * N * nI] : nullptr;   // product buffers (xy classes)
-  // contracted [e0|f0] and the transfer relations are FP64 in both paths: the FP32 path
-  // hands its contracted values over before the transfer, whose cancellations grow with |A-B|
-  double* scr = a.scratch + gteam * c.scratch_per_team;
-  double* E0 = scr;                                  // [ne][nf] contracted [e0|f0]
-  double* bufA = scr + c.nout;
-  double* bufB = bufA + c.hrr_doubles;
-
-  unsigned long long cnt_q = 0, cnt_p = 0;
-
-  const bool listed = (a.mode == KMODE_JK) && (a.tlist != nullptr || a.jobs != nullptr);
-  const long long ntask = listed ? (long long)*a.tcount : a.ntask;
-
-  while (true) {
-    // ---- fetch TEAMS_PER_WARP tasks per warp
-    unsigned long long tbase = 0;
-    if (lane == 0) tbase = atomicAdd(a.counter, (unsigned long long)TEAMS_PER_WARP);
-    tbase = __shfl_sync(0xffffffffu, tbase, 0);
-    if (tbase >= (unsigned long long)ntask) break;
-    const long long task = (long long)tbase + lane / TS;
-    bool active = task < ntask;
-
-    // ---- decode the task into (bra pair, ket pair)
-    int ib = 0, ik = 0;
-    TaskCtx tc = single_ctx(a);
-    if (active) {
-      if (a.mode != KMODE_JK) {
-        ib = a.tasklist[2 * task];
-        ik = a.tasklist[2 * task + 1];
-      } else {
-        resolve_task(a, task, listed, tc, ib, ik);
-      }
-    }
-    const PP* prims_r = reinterpret_cast<const PP*>(sizeof(R) == 8 ? (const void*)tc.prims : (const void*)tc.primsf);
-    const ShellPair* bra = tc.pairs + ib;
-    const ShellPair* ket = tc.pairs + ik;
-    // ---- screening (Eqs. 7-9) and, in the mixed mode, the precision split
-    //      (quartet_category).  Listed tasks were screened by the compaction.
-    if (active && a.mode == KMODE_JK && !listed) {
-      const int cat = quartet_category(a, bra, ket, a.prec_sel != 0);
-      active = cat != 0 && (a.prec_sel == 0 || cat == a.prec_sel);
-    }
-    const int npb = active ? bra->nprim : 0;
-    const int npk = active ? ket->nprim : 0;
-    const int nq = npb * npk;
-    const int maxq = warp_max(nq);
-    if (tl == 0 && active) { cnt_q += 1; cnt_p += (unsigned long long)nq; }
-
-    double AB[3], CD[3];
-    if (active) {
-      AB[0] = bra->AB[0]; AB[1] = bra->AB[1]; AB[2] = bra->AB[2];
-      CD[0] = ket->AB[0]; CD[1] = ket->AB[1]; CD[2] = ket->AB[2];
-    }
-    const int boff = active ? bra->prim_off : 0, koff = active ? ket->prim_off : 0;
-
-    for (int pass = 0; pass < npass; ++pass) {
-      // ---- my output slots for this pass
-      const int o0 = pass * TS * GSLOTS;
-      uint32_t pkd[GSLOTS];
-      R acc[GSLOTS];
-#pragma unroll
-      for (int k = 0; k < GSLOTS; ++k) {
-        const int o = o0 + k * TS + tl;
-        // TS = 1: every lane has the same slots, so the index is re-read (broadcast) instead
-        if (TS > 1) pkd[k] = (o < nslot) ? __ldg(outidx + o) : (1u << 31);
-        acc[k] = R(0);
-      }
-      const int kcnt = min(GSLOTS, (nslot - o0 + TS - 1) / TS);     // uniform
-      const uint32_t gm = XY ? 0u : __ldg(c.gmask + pass);           // group starts (uniform)
-      const uint32_t* xyt = nullptr;                 // products of this pass (xy classes)
-      int ncp = 0;
-      uint32_t xq[XY ? XQ : 1];                      // this lane's first product indices
-      if (XY) {
-        xyt = c.xytab + __ldg(c.passinfo + 2 * pass);
-        ncp = (int)__ldg(c.passinfo + 2 * pass + 1);
-#pragma unroll
-        for (int i = 0; i < XQ; ++i) {
-          const int t = tl + i * TS;
-          xq[i] = (t < ncp) ? __ldg(xyt + t) : 0u;
-        }
-      }
-
-      for (int q0 = 0; q0 < maxq; q0 += bp) {
-        const int nbt = min(bp, nq - q0);            // this team's primitives in the batch (may be <= 0)
-        // ---- a. primitive-quartet scalars: T and the table lookup in FP64, the rest in R
-        for (int j = tl; j < bp; j += TS) {
-          if (j < nbt) {
-            const int q = q0 + j;
-            const int ixp = boff + q / npk, iyp = koff + q % npk;
-            const PrimPair* xd = tc.prims + ixp;
-            const PrimPair* yd = tc.prims + iyp;
-            const double s = xd->zeta + yd->zeta;
-            const double rd = rsqrt(s);
-            const double PQ0 = xd->P[0] - yd->P[0], PQ1 = xd->P[1] - yd->P[1], PQ2 = xd->P[2] - yd->P[2];
-            const double T = xd->zeta * yd->zeta * (rd * rd) * fma(PQ0, PQ0, fma(PQ1, PQ1, PQ2 * PQ2));
-            int ti;
-            double xx, invT, rsqT;
-            rys_locate(T, a.rys_tcut_d, ti, xx, invT, rsqT);
-            const int od = j * NPD;
-            sd[od + 0] = xx;
-            sd[od + 1] = invT;
-            sd[od + 2] = rsqT;
-            sd[od + 3] = __longlong_as_double((long long)ti);
-            const PP* x = (sizeof(R) == 8) ? reinterpret_cast<const PP*>(xd) : prims_r + ixp;
-            const PP* y = (sizeof(R) == 8) ? reinterpret_cast<const PP*>(yd) : prims_r + iyp;
-            const R zeta = x->zeta, eta = y->zeta;
-            // P - Q and 1/sqrt(zeta + eta) from their FP64 values (P - Q formed in FP32 from
-            // rounded centres would carry an absolute error of ~|P| 6e-8 bohr)
-            const R r = (R)rd, P0 = (R)PQ0, P1 = (R)PQ1, P2 = (R)PQ2;
-            const R inv_s = r * r;
-            const R rz = eta * inv_s, re = zeta * inv_s;
-            const R hz = x->hz, he = y->hz;
-            const int o = j * NPR;
-            sr[o + 0] = x->PA[0]; sr[o + 1] = x->PA[1]; sr[o + 2] = x->PA[2];
-            sr[o + 3] = y->PA[0]; sr[o + 4] = y->PA[1]; sr[o + 5] = y->PA[2];
-            sr[o + 6] = rz * P0; sr[o + 7] = rz * P1; sr[o + 8] = rz * P2;
-            sr[o + 9] = re * P0; sr[o + 10] = re * P1; sr[o + 11] = re * P2;
-            sr[o + 12] = R(0.5) * inv_s;
-            sr[o + 13] = hz * rz;
-            sr[o + 14] = he * re;
-            sr[o + 15] = x->E * y->E * r;             // Theta with contraction coefficients
-            sr[o + 16] = hz;
-            sr[o + 17] = he;
-          }
-        }
-        __syncwarp();
-        // ---- b. roots, weights (FP64) and 2D integrals (R) per (primitive, root), or per
-        //      (primitive, root, axis) when that fills more of the team's lanes
-        if (TS > 1 && (XY ? c.split3_xy : c.split3)) {
-          for (int tk = tl; tk < bp * N * 3; tk += TS) {
-            const int jn = tk / 3, ax = tk - jn * 3;
-            const int j = jn / N, n = jn - (jn / N) * N;
-            if (j < nbt) {
-              const int od = j * NPD, o = j * NPR;
-              double ud, wd;
-              rys_root(a.rys_coef, a.rys_au, a.rys_aw, N, (int)__double_as_longlong(sd[od + 3]), sd[od + 0],
-                       sd[od + 1], sd[od + 2], n, ud, wd);
-              const R u = (R)ud;
-              const R B00 = u * sr[o + 12];
-              const R B10 = fma(-u, sr[o + 13], sr[o + 16]);
-              const R B01 = fma(-u, sr[o + 14], sr[o + 17]);
-              const R Cax = fma(-u, sr[o + 6 + ax], sr[o + 0 + ax]);
-              const R Cpx = fma(u, sr[o + 9 + ax], sr[o + 3 + ax]);
-              const R I00 = (ax == 2) ? (R)wd * sr[o + 15] : R(1);
-              rys_2d1<R>(sr, S_2D + ((j * 3 + ax) * N + n) * nI, Le, Lf, I00, Cax, Cpx, B00, B10, B01);
-            }
-          }
-        } else {
-          for (int tk = tl; tk < bp * N; tk += TS) {
-            const int j = tk / N, n = tk - (tk / N) * N;
-            if (j < nbt) {
-              const int od = j * NPD, o = j * NPR;
-              double ud, wd;
-              rys_root(a.rys_coef, a.rys_au, a.rys_aw, N, (int)__double_as_longlong(sd[od + 3]), sd[od + 0],
-                       sd[od + 1], sd[od + 2], n, ud, wd);
-              const R u = (R)ud, w = (R)wd;
-              const R B00 = u * sr[o + 12];
-              const R B10 = fma(-u, sr[o + 13], sr[o + 16]);
-              const R B01 = fma(-u, sr[o + 14], sr[o + 17]);
-              const R wt = w * sr[o + 15];
-              const R C[3] = {fma(-u, sr[o + 6], sr[o + 0]), fma(-u, sr[o + 7], sr[o + 1]),
-                              fma(-u, sr[o + 8], sr[o + 2])};
-              const R Cp[3] = {fma(u, sr[o + 9], sr[o + 3]), fma(u, sr[o + 10], sr[o + 4]),
-                               fma(u, sr[o + 11], sr[o + 5])};
-              const int g0 = S_2D + ((j * 3 + 0) * N + n) * nI;
-              const int og[3] = {g0, g0 + N * nI, g0 + 2 * N * nI};
-              rys_2d3<R>(sr, og, Le, Lf, wt, C, Cp, B00, B10, B01);
-            }
-          }
-        }
-        __syncwarp();
-        // ---- c. assembly of [e0|f0] (Eq. 1) and contraction (Eq. 5) in registers
-        if (XY) {
-          // products path: per (primitive, root) step the team forms this pass's distinct
-          // I_x I_y products once, then each value is one FMA with I_z.  Software-pipelined
-          // over steps: the products of step s+1 (buffer (s+1)&1) are formed while the FMAs
-          // of step s read buffer s&1, with one warp synchronisation per step.  Steps of a
-          // team past its primitive count compute on stale (in-bounds) table entries and
-          // leave the accumulators unchanged.
-          const int nsteps = warp_max(nbt) * N;
-          auto form = [&](int st) {
-            const int jj = st / N, nn = st - (st / N) * N;
-            const int gx = S_2D + ((jj * 3 + 0) * N + nn) * nI;
-            const int gy = gx + N * nI;
-            R* buf = xyb + (st & 1) * c.xymax;
-#pragma unroll
-            for (int i = 0; i < XQ; ++i) {
-              const int t = tl + i * TS;
-              if (t < ncp) buf[t] = sr[gx + (int)(xq[i] & 0xffu)] * sr[gy + (int)((xq[i] >> 8) & 0xffu)];
-            }
-            for (int t = tl + XQ * TS; t < ncp; t += TS) {
-              const uint32_t q = __ldg(xyt + t);
-              buf[t] = sr[gx + (int)(q & 0xffu)] * sr[gy + (int)((q >> 8) & 0xffu)];
-            }
-          };
-          if (nsteps > 0) form(0);
-          __syncwarp();
-          for (int st = 0; st < nsteps; ++st) {
-            if (st + 1 < nsteps) form(st + 1);
-            const int jj = st / N, nn = st - (st / N) * N;
-            const bool jv = jj < nbt;
-            const int gz = S_2D + ((jj * 3 + 2) * N + nn) * nI;
-            const R* buf = xyb + (st & 1) * c.xymax;
-#pragma unroll
-            for (int k = 0; k < GSLOTS; ++k) {
-              if (k < kcnt) {
-                const uint32_t p = pkd[k];
-                const R v = fma(buf[(int)(p & 0xffffu)], sr[gz + (int)((p >> 16) & 0xffu)], acc[k]);
-                acc[k] = jv ? v : acc[k];
-              }
-            }
-            __syncwarp();
-          }
-        } else {
-          // lane programs: a slot that starts a group forms the group's I_x I_y product, the
-          // rest of the group reuses it; the start bits are the same for every lane
-          for (int j = 0; j < bp; ++j) {
-            if (j < nbt) {
-              for (int n = 0; n < N; ++n) {
-                const int gx = S_2D + ((j * 3 + 0) * N + n) * nI;
-                const int gy = gx + N * nI;
-                const int gz = gy + N * nI;
-                R v = R(0);
-#pragma unroll
-                for (int k = 0; k < GSLOTS; ++k) {
-                  if (k < kcnt) {
-                    const uint32_t p = (TS == 1) ? __ldg(outidx + o0 + k) : pkd[k];
-                    if ((gm >> k) & 1u) v = sr[gx + (int)(p & 0xffu)] * sr[gy + (int)((p >> 8) & 0xffu)];
-                    acc[k] = fma(v, sr[gz + (int)((p >> 16) & 0xffu)], acc[k]);
-                  }
-                }
-              }
-            }
-          }
-        }
-        __syncwarp();
-      }
-      // ---- contracted values of this pass -> team scratch ([e][f] order)
-      if (active) {
-#pragma unroll
-        for (int k = 0; k < GSLOTS; ++k) {
-          const int o = o0 + k * TS + tl;
-          if (k < kcnt && o < nslot) {
-            const uint32_t p = (TS == 1) ? __ldg(outidx + o0 + k) : pkd[k];
-            if (XY || !(p >> 31)) E0[(int)__ldg(dsttab + o)] = (double)acc[k];
-          }
-        }
-      }
-    }
-    __syncwarp();
-
-    finish_quartet<TS, double>(a, tc, c, E0, bufA, bufB, tl, active, AB, CD, bra, ket, ib, ik, task);
-    __syncwarp();
-  }
-  // ---- counters: one atomic pair per warp
-  for (int off = 16; off > 0; off >>= 1) {
-    cnt_q += __shfl_xor_sync(0xffffffffu, cnt_q, off);
-    cnt_p += __shfl_xor_sync(0xffffffffu, cnt_p, off);
-  }
-  if (lane == 0 && a.stats) {
-    atomicAdd(a.stats + 0, cnt_q);
-    atomicAdd(a.stats + 1, cnt_p);
-  }
-}
-
 // ------------------------------------------------------------------ helper kernels
 // Dmax[I][J] = max over densities and a in I, b in J of |D_ab| (Eq. 9's block maxima).
 __global__ void dmax_kernel(const double* __restrict__ D, int nD, int nbf, int nsh,
@@ -486,6 +183,32 @@ __global__ void dmax_kernel(const double* __restrict__ D, int nD, int nbf, int n
       for (int b = 0; b < nfun[Jsh]; ++b)
         m = fmax(m, fabs(D[(size_t)x * nbf * nbf + (size_t)(bf0[I] + a) * nbf + bf0[Jsh] + b]));
   Dmax[t] = m;
+}
+
+// out[0] = max over densities of |D_ij - D_ji|, out[1] = max |D_ij|, as the bit patterns of
+// non-negative doubles (which order like unsigned integers, so atomicMax applies).
+__global__ void symcheck_kernel(const double* __restrict__ D, int nD, int nbf, unsigned long long* out) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long per = (long long)nbf * nbf;
+  double asym = 0.0, mx = 0.0;
+  if (t < per * nD) {
+    const int x = (int)(t / per);
+    const long long r = t % per;
+    const int i = (int)(r / nbf), j = (int)(r % nbf);
+    const double* Dx = D + (size_t)x * per;
+    const double a = Dx[(size_t)i * nbf + j];
+    mx = fabs(a);
+    if (j > i) asym = fabs(a - Dx[(size_t)j * nbf + i]);
+    if (!(mx <= 1.7e308)) { mx = __longlong_as_double(0x7ff0000000000000LL); asym = mx; }  // NaN / inf
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    asym = fmax(asym, __shfl_xor_sync(0xffffffffu, asym, off));
+    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(out + 0, (unsigned long long)__double_as_longlong(asym));
+    atomicMax(out + 1, (unsigned long long)__double_as_longlong(mx));
+  }
 }
 
 // M <- M + M^T in place for every density (J = J~ + J~^T, K = K~ + K~^T).
@@ -572,6 +295,9 @@ extern "C" int erik_launch_class(int ts, int fp32, const KernelArgs* a, int grid
   cudaStream_t s = (cudaStream_t)stream;
   const bool xy = a->c.xy != 0 && !fp32;
   if (xy && ts == 1) return (int)cudaErrorInvalidValue;
+  // a kernel compiled for this class, team size and assembly path, where one exists
+  int rc = 0;
+  if (!fp32 && erik_launch_class_spec(ts, xy ? 1 : 0, a, grid, smem_bytes, stream, &rc)) return rc;
 #define CLASS_LAUNCH(T, R)                                                                     \
   if (xy)                                                                                      \
     eri_class_kernel<T, R, (T > 1 && sizeof(R) == 8)><<<grid, TPB, smem_bytes, s>>>(*a);      \
@@ -629,6 +355,13 @@ extern "C" int erik_launch_dmax(const double* D, int nD, int nbf, int nsh, const
   const long long n = (long long)nsh * nsh;
   const int grid = (int)((n + 255) / 256);
   dmax_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(D, nD, nbf, nsh, sh_bf0, sh_n, Dmax);
+  return (int)cudaGetLastError();
+}
+
+extern "C" int erik_launch_symcheck(const double* D, int nD, int nbf, unsigned long long* out, void* stream) {
+  const long long n = (long long)nbf * nbf * nD;
+  const int grid = (int)((n + 255) / 256);
+  symcheck_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(D, nD, nbf, out);
   return (int)cudaGetLastError();
 }
 

@@ -107,10 +107,11 @@ int choose_ts(int nout) {
 // so two blocks fit on an SM.
 int team_budget(int ts) { return ts == 2 ? 192 : ts == 4 ? 384 : ts == 8 ? 768 : 3072; }
 
-// Per-class overrides of the team size and the products path: "la lb lc ld ts xy" entries
-// separated by ';' in ERI_CLASS_CONFIG (xy -1 = automatic), read once per process.  For
-// tuning the choice on new hardware.
-struct ClassTune { int ts = -1, xy = -1; };
+// Per-class overrides of the team size, the products path and the staging of pair records:
+// "la lb lc ld ts xy [stage]" entries separated by ';' in ERI_CLASS_CONFIG (xy -1 = automatic;
+// stage 1 = bulk-copy staging, where a kernel compiled for the class has it), read once per
+// process.  For tuning the choices on new hardware.
+struct ClassTune { int ts = -1, xy = -1, stage = 0; };
 ClassTune class_tune(int la, int lb, int lc, int ld) {
   static std::vector<std::vector<int>> table;
   static bool read = false;
@@ -122,8 +123,10 @@ ClassTune class_tune(int la, int lb, int lc, int ld) {
       while (pos < str.size()) {
         size_t end = str.find(';', pos);
         if (end == std::string::npos) end = str.size();
-        std::vector<int> v(6, -1);
-        if (sscanf(str.substr(pos, end - pos).c_str(), "%d %d %d %d %d %d", &v[0], &v[1], &v[2], &v[3], &v[4], &v[5]) >= 5)
+        std::vector<int> v(7, -1);
+        v[6] = 0;
+        if (sscanf(str.substr(pos, end - pos).c_str(), "%d %d %d %d %d %d %d", &v[0], &v[1], &v[2], &v[3], &v[4], &v[5],
+                   &v[6]) >= 5)
           table.push_back(v);
         pos = end + 1;
       }
@@ -141,6 +144,7 @@ ClassTune class_tune(int la, int lb, int lc, int ld) {
     if (v[0] == la && v[1] == lb && v[2] == lc && v[3] == ld) {
       if (v[4] == 1 || v[4] == 2 || v[4] == 4 || v[4] == 8 || v[4] == 32) t.ts = v[4];
       t.xy = v[5];
+      t.stage = v[6] == 1 ? 1 : 0;
     }
   return t;
 }
@@ -244,6 +248,7 @@ void make_class(int la, int lb, int lc, int ld, ClassDesc* c, int* ts, std::vect
   const int L1 = c->Lf + 1;
   const ClassTune tune = class_tune(la, lb, lc, ld);
   *ts = tune.ts > 0 ? tune.ts : choose_ts(c->nout);
+  c->stage = (tune.stage && *ts == 8 && la == 2 && lb == 1 && lc == 2 && ld == 1) ? 1 : 0;
   const int T = *ts;
   const int per_pass = T * 32;
 
@@ -484,6 +489,8 @@ eri_status device_init(int dev, DeviceState** out) {
     CUDA_TRY(erik_upload_cart_tables());
     CUDA_TRY(erik_upload_cart_tables_small());
     CUDA_TRY(erik_upload_cart_tables_grad());
+    CUDA_TRY(erik_upload_cart_tables_spec());
+    CUDA_TRY(erik_class_spec_prepare());
     size_t ncoef = (size_t)RYS_NCOEF, nas = (size_t)RYS_ASYM_OFFSET[RYS_NMAX] + RYS_NMAX;
     CUDA_TRY(cudaMalloc(&s.rys_coef, sizeof(double) * ncoef));
     CUDA_TRY(cudaMalloc(&s.rys_au, sizeof(double) * nas));
@@ -658,6 +665,8 @@ struct eri_plan {
   unsigned long long* d_tcount = nullptr;     // [256][2] FP64 / FP32 list lengths
   unsigned* d_tiles = nullptr;                // per-tile counts / offsets of the compaction
   unsigned long long* d_gstats = nullptr;     // [2] quartets / primitive quartets of eri_jk_grad
+  unsigned long long* d_symchk = nullptr;     // [2] max|D_ij - D_ji|, max|D| (check_symmetric)
+  unsigned* d_err = nullptr;                  // set by a kernel whose bounded device wait gave up
   cudaStream_t grad_stream = nullptr;
   // second stream of eri_jk: classes alternate between the caller's stream and this one,
   // each with its own half of the task lists, tile counts and scratch
@@ -713,6 +722,8 @@ eri_status launch_shape(eri_plan* p, int X, int Y, int fp32, long long nteams_ne
   const int teams_per_block = 128 / ts;
   *smem = (int)(sizeof(double) * (size_t)(fp32 ? c.team_doubles_f32 : (c.xy ? c.team_doubles_xy : c.team_doubles)) *
                 teams_per_block);
+  // staged FP64 launches: per team STAGE_REC 80-byte pair records and an mbarrier, 16-aligned
+  if (c.stage && !fp32) *smem = ((*smem + 15) & ~15) + teams_per_block * (20 * (int)sizeof(PrimPair) + 8);
   if (*smem > 200 * 1024) return fail(ERI_ERR_ARG, "class (%d%d|%d%d) needs %d bytes of shared memory", c.la, c.lb, c.lc, c.ld, *smem);
   int bps = 0;
   CUDA_TRY(erik_blocks_per_sm(ts, fp32, (c.xy && !fp32) ? 1 : 0, *smem, &bps));
@@ -738,6 +749,7 @@ KernelArgs base_args(eri_plan* p, int X, int Y) {
   a.rys_aw = p->dev->rys_aw + RYS_ASYM_OFFSET[N];
   a.rys_tcut = RYS_TCUT[N];
   a.rys_tcut_d = (double)RYS_TCUT[N];
+  a.err = p->d_err;
   return a;
 }
 
@@ -803,6 +815,7 @@ struct Launch {
   int X, Y, fp32, grid, smem, ts;
   long long nt;
   int small;             // 1: compile-time specialised kernel (eri_small.cu)
+  int split;             // 1: the class runs an FP64 and an FP32 launch (mixed mode)
 };
 
 eri_status check_jk_args(eri_plan* p, const double* D, int nD, double* J, double* K, int flags) {
@@ -814,6 +827,15 @@ eri_status check_jk_args(eri_plan* p, const double* D, int nD, double* J, double
   if ((want & 1) && !J) return fail(ERI_ERR_ARG, "J requested but NULL");
   if ((want & 2) && !K) return fail(ERI_ERR_ARG, "K requested but NULL");
   return ERI_OK;
+}
+
+// In the mixed mode, whether class (X|Y) gets an FP32 launch: its task space must reach the
+// plan's mixed_min_tasks (a second launch for a handful of quartets costs more than the FP32
+// arithmetic saves); otherwise every quartet of the class runs in FP64.
+bool fp32_pays(const eri_plan* p, int X, int Y, long long nt) {
+  (void)X;
+  (void)Y;
+  return nt >= (long long)p->opts.mixed_min_tasks;
 }
 
 // One launch per class (pair-type pair X >= Y); in the mixed mode one FP64 and one FP32
@@ -828,8 +850,9 @@ eri_status plan_launches(eri_plan* p, size_t max_scratch, std::vector<Launch>* o
       if (!p->type_cnt[Y]) continue;
       const long long nx = p->type_cnt[X], ny = p->type_cnt[Y];
       const long long nt = (X == Y) ? nx * (nx + 1) / 2 : nx * ny;
-      for (int fp32 = 0; fp32 < nprec; ++fp32) {
-        Launch l{X, Y, fp32, 0, 0, 0, nt, 0};
+      const int np = (nprec == 2 && fp32_pays(p, X, Y, nt)) ? 2 : 1;
+      for (int fp32 = 0; fp32 < np; ++fp32) {
+        Launch l{X, Y, fp32, 0, 0, 0, nt, 0, np == 2 ? 1 : 0};
         eri_status s = launch_shape(p, X, Y, fp32, nt, &l.grid, &l.smem, &l.ts);
         if (s != ERI_OK) return s;
         const ClassDesc& cd = p->dev->classes[X][Y];
@@ -898,13 +921,13 @@ eri_status run_jk(eri_plan* p, const std::vector<Launch>& launches, const double
       p->events.push_back(e);
     }
   }
-  if (record) {
-    p->last_launch_xy.clear();
-    p->last_launch_ts.clear();
-    p->last_launch_grid.clear();
-    p->last_launch_fp32.clear();
-    p->last_launch_small.clear();
-  }
+  // an unrecorded call (eri_jk_noalloc) leaves no records, so eri_launch_records never mixes
+  // an earlier call's launches with this call's counters
+  p->last_launch_xy.clear();
+  p->last_launch_ts.clear();
+  p->last_launch_grid.clear();
+  p->last_launch_fp32.clear();
+  p->last_launch_small.clear();
   if (nstreams == 2) {
     CUDA_TRY(cudaEventRecord(p->ev_fork, st));
     CUDA_TRY(cudaStreamWaitEvent(p->side, p->ev_fork, 0));
@@ -929,7 +952,7 @@ eri_status run_jk(eri_plan* p, const std::vector<Launch>& launches, const double
     a.ntask = l.nt;
     a.Dmax = p->d_Dmax;
     a.tau = p->opts.screen_thresh;
-    a.prec_sel = mixed ? (l.fp32 ? 2 : 1) : 0;
+    a.prec_sel = l.split ? (l.fp32 ? 2 : 1) : 0;
     a.mixed_thr = p->opts.mixed_thresh;
     a.D = D;
     a.J = J;
@@ -944,7 +967,7 @@ eri_status run_jk(eri_plan* p, const std::vector<Launch>& launches, const double
     if (listed) {
       unsigned long long* cnt = p->d_tcount + 2 * ci;
       if (!l.fp32)
-        CUDA_TRY(erik_launch_compact(&a, tlist_l, (unsigned long long)l.nt, cnt, tiles_l, mixed ? 1 : 0, sl));
+        CUDA_TRY(erik_launch_compact(&a, tlist_l, (unsigned long long)l.nt, cnt, tiles_l, l.split, sl));
       a.tlist = tlist_l;
       a.list_cap = (unsigned long long)l.nt;
       a.from_back = l.fp32;
@@ -979,6 +1002,54 @@ eri_status run_jk(eri_plan* p, const std::vector<Launch>& launches, const double
   p->last_want = want;
   return ERI_OK;
 }
+
+// eri_jk's launches and the sizes of its buffers: scratch per stream (need doubles), task
+// list per stream (maxnt) and tile counts per stream (tiles).  Everything depends on the
+// plan alone, so the buffers are allocated once, at plan creation, and no eri_jk call
+// allocates (ensure_* find them large enough).  The side stream and its events too.
+eri_status size_jk_buffers(eri_plan* p, std::vector<Launch>* launches, size_t* need_out, size_t* maxnt_out,
+                           size_t* tiles_out) {
+  eri_status s;
+  if ((s = plan_launches(p, 0, launches)) != ERI_OK) return s;
+  size_t need = 0;
+  for (const Launch& l : *launches)
+    need = std::max(need, (size_t)l.grid * (size_t)(128 / l.ts) * (size_t)p->dev->classes[l.X][l.Y].scratch_per_team);
+  need = (need + 31) & ~(size_t)31;
+  size_t maxnt = 1;
+  for (const Launch& l : *launches)
+    if ((unsigned long long)l.nt <= 0xffffffffULL) maxnt = std::max(maxnt, (size_t)l.nt);
+  maxnt = (maxnt + 31) & ~(size_t)31;
+  const size_t tiles = 2 * ((maxnt + 1023) / 1024 + 1);
+  // two streams, each with its own half of scratch, task lists and tile counts
+  if ((s = ensure_scratch(p, 2 * need)) != ERI_OK) return s;
+  if ((s = ensure_buf(&p->d_tlist, &p->tlist_cap, 2 * maxnt)) != ERI_OK) return s;
+  if ((s = ensure_buf(&p->d_tiles, &p->tiles_cap, 2 * tiles)) != ERI_OK) return s;
+  if (!p->side) {
+    CUDA_TRY(cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking));
+    CUDA_TRY(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
+    CUDA_TRY(cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming));
+  }
+  *need_out = need;
+  *maxnt_out = maxnt;
+  *tiles_out = tiles;
+  return ERI_OK;
+}
+
+// Symmetry of the densities on the device (the plan's check_symmetric option): max|D_ij - D_ji|
+// against 1e-12 max|D|; synchronises the stream.  The plan's d_symchk holds the two maxima.
+eri_status check_density_device(eri_plan* p, const double* D, int nD, cudaStream_t st) {
+  unsigned long long h[2] = {0, 0};
+  CUDA_TRY(cudaMemsetAsync(p->d_symchk, 0, sizeof(h), st));
+  CUDA_TRY(erik_launch_symcheck(D, nD, p->nbf, p->d_symchk, st));
+  CUDA_TRY(cudaMemcpyAsync(h, p->d_symchk, sizeof(h), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  double asym, mx;
+  memcpy(&asym, &h[0], sizeof(double));
+  memcpy(&mx, &h[1], sizeof(double));
+  if (!(asym <= 1e-12 * mx))
+    return fail(ERI_ERR_ARG, "D is not symmetric: max|D_ij - D_ji| = %.3e, max|D| = %.3e", asym, mx);
+  return ERI_OK;
+}
 }  // namespace
 
 // ================================================================= C-ABI
@@ -998,7 +1069,7 @@ eri_status eri_plan_destroy(eri_plan* p) {
   if (p->ev_join) cudaEventDestroy(p->ev_join);
   void* bufs[] = {p->d_pairs_all, p->d_pairs, p->d_prims, p->d_primsf, p->d_sh_bf0, p->d_sh_n, p->d_sh_atom, p->d_Dmax, p->d_counters,
                   p->d_stats, p->d_scratch, p->d_tasks, p->d_out, p->d_off, p->d_host_io, p->d_tlist,
-                  p->d_tcount, p->d_tiles, p->d_gstats};
+                  p->d_tcount, p->d_tiles, p->d_gstats, p->d_symchk, p->d_err};
   for (void* b : bufs)
     if (b) cudaFree(b);
   delete p;
@@ -1014,6 +1085,8 @@ eri_status eri_plan_create(const eri_basis* basis, const eri_opts* opts, void* c
     return fail(ERI_ERR_ARG, "screen_thresh must be finite and >= 0");
   if (opts->max_nd < 1) return fail(ERI_ERR_ARG, "max_nd must be >= 1");
   if (opts->precision != ERI_FP64 && opts->precision != ERI_MIXED) return fail(ERI_ERR_ARG, "unknown precision mode");
+  if (opts->check_symmetric != 0 && opts->check_symmetric != 1) return fail(ERI_ERR_ARG, "check_symmetric must be 0 or 1");
+  if (opts->mixed_min_tasks < 0) return fail(ERI_ERR_ARG, "mixed_min_tasks must be >= 0");
   eri_status s = validate_basis(basis);
   if (s != ERI_OK) return s;
   int ndev = 0;
@@ -1137,7 +1210,9 @@ eri_status eri_plan_create(const eri_basis* basis, const eri_opts* opts, void* c
       cudaMalloc(&p->d_Dmax, sizeof(double) * p->nshell * p->nshell) != cudaSuccess ||
       cudaMalloc(&p->d_counters, sizeof(unsigned long long) * 256) != cudaSuccess ||
       cudaMalloc(&p->d_stats, sizeof(unsigned long long) * 4 * 256) != cudaSuccess ||
-      cudaMalloc(&p->d_tcount, sizeof(unsigned long long) * 2 * 256) != cudaSuccess) {
+      cudaMalloc(&p->d_tcount, sizeof(unsigned long long) * 2 * 256) != cudaSuccess ||
+      cudaMalloc(&p->d_symchk, sizeof(unsigned long long) * 2) != cudaSuccess ||
+      cudaMalloc(&p->d_err, sizeof(unsigned)) != cudaSuccess) {
     cudaGetLastError();
     return cleanup(fail(ERI_ERR_OOM, "device allocation failed in eri_plan_create"));
   }
@@ -1159,11 +1234,12 @@ eri_status eri_plan_create(const eri_basis* basis, const eri_opts* opts, void* c
     f.hz = (float)x.hz;
     f.pad[0] = f.pad[1] = 0.f;
   }
-  PLAN_TRY(cudaMemcpy(p->d_primsf, primsf.data(), sizeof(PrimPairF) * primsf.size(), cudaMemcpyHostToDevice));
+  PLAN_TRY(cudaMemcpyAsync(p->d_primsf, primsf.data(), sizeof(PrimPairF) * primsf.size(), cudaMemcpyHostToDevice, st));
   PLAN_TRY(cudaMemcpyAsync(p->d_sh_bf0, p->sh_bf0.data(), sizeof(int) * p->nshell, cudaMemcpyHostToDevice, st));
   PLAN_TRY(cudaMemcpyAsync(p->d_sh_n, sh_n.data(), sizeof(int) * p->nshell, cudaMemcpyHostToDevice, st));
   PLAN_TRY(cudaMemcpyAsync(p->d_sh_atom, p->sh_atom.data(), sizeof(int) * p->nshell, cudaMemcpyHostToDevice, st));
   PLAN_TRY(cudaMemsetAsync(p->d_stats, 0, sizeof(unsigned long long) * 4 * 256, st));
+  PLAN_TRY(cudaMemsetAsync(p->d_err, 0, sizeof(unsigned), st));
 
   // ---- Schwarz factors (Eq. 7) from the diagonal quartets (ij|ij), one class (X|X) at a time;
   // the same launches give max_e [e0|e0] before the transfer relations, for the mixed mode's
@@ -1212,6 +1288,12 @@ eri_status eri_plan_create(const eri_basis* basis, const eri_opts* opts, void* c
     PLAN_TRY(cudaMemcpyAsync(p->d_pairs, kept.data(), sizeof(ShellPair) * kept.size(), cudaMemcpyHostToDevice, st));
   PLAN_TRY(cudaStreamSynchronize(st));
 #undef PLAN_TRY
+  {
+    // eri_jk's scratch, task lists and tile counts, sized now from the plan alone
+    std::vector<Launch> launches;
+    size_t need, maxnt, tiles;
+    if ((s = size_jk_buffers(p, &launches, &need, &maxnt, &tiles)) != ERI_OK) return cleanup(s);
+  }
   *out = p;
   return ERI_OK;
 }
@@ -1221,20 +1303,9 @@ eri_status eri_jk(eri_plan* p, const double* D, int nD, double* J, double* K, in
   eri_status s = check_jk_args(p, D, nD, J, K, flags);
   if (s != ERI_OK) return s;
   std::vector<Launch> launches;
-  if ((s = plan_launches(p, 0, &launches)) != ERI_OK) return s;
-  size_t need = 0;
-  for (const Launch& l : launches)
-    need = std::max(need, (size_t)l.grid * (size_t)(128 / l.ts) * (size_t)p->dev->classes[l.X][l.Y].scratch_per_team);
-  need = (need + 31) & ~(size_t)31;
-  size_t maxnt = 1;
-  for (const Launch& l : launches)
-    if ((unsigned long long)l.nt <= 0xffffffffULL) maxnt = std::max(maxnt, (size_t)l.nt);
-  maxnt = (maxnt + 31) & ~(size_t)31;
-  const size_t tiles = 2 * ((maxnt + 1023) / 1024 + 1);
-  // two streams, each with its own half of scratch, task lists and tile counts
-  if ((s = ensure_scratch(p, 2 * need)) != ERI_OK) return s;
-  if ((s = ensure_buf(&p->d_tlist, &p->tlist_cap, 2 * maxnt)) != ERI_OK) return s;
-  if ((s = ensure_buf(&p->d_tiles, &p->tiles_cap, 2 * tiles)) != ERI_OK) return s;
+  size_t need, maxnt, tiles;
+  if ((s = size_jk_buffers(p, &launches, &need, &maxnt, &tiles)) != ERI_OK) return s;
+  if (p->opts.check_symmetric && (s = check_density_device(p, D, nD, (cudaStream_t)cuda_stream)) != ERI_OK) return s;
   return run_jk(p, launches, D, nD, J, K, flags & 3, (cudaStream_t)cuda_stream, p->d_scratch, true, true, 2, maxnt,
                 tiles, need);
 }
@@ -1369,8 +1440,9 @@ eri_status eri_jk_host(eri_plan* p, const double* D, int nD, double* J, double* 
   if ((want & 2) && !K) return fail(ERI_ERR_ARG, "K requested but NULL");
   cudaStream_t st = (cudaStream_t)cuda_stream;
   const size_t mat = (size_t)nD * p->nbf * p->nbf;
-  eri_status s = ensure_buf(&p->d_host_io, &p->host_io_cap, 3 * mat);
-  if (s != ERI_OK) return s;
+  eri_status s;
+  if (p->opts.check_symmetric && (s = eri_check_density(D, nD, p->nbf)) != ERI_OK) return s;
+  if ((s = ensure_buf(&p->d_host_io, &p->host_io_cap, 3 * mat)) != ERI_OK) return s;
   double* dD = p->d_host_io;
   double* dJ = dD + mat;
   double* dK = dJ + mat;
@@ -1490,6 +1562,29 @@ eri_status eri_flop_stats(eri_plan* p, eri_stats* out) {
   out->npairs_total = (int)p->pairs_all.size();
   out->npairs_kept = p->npairs_kept;
   out->nclasses_launched = p->last_nclasses;
+  unsigned err = 0;
+  CUDA_TRY(cudaMemcpy(&err, p->d_err, sizeof(err), cudaMemcpyDeviceToHost));
+  out->device_status = (int)err;
+  if (err) return fail(ERI_ERR_TIMEOUT, "a bounded device wait of the plan's kernels gave up");
+  return ERI_OK;
+}
+
+eri_status eri_check_density(const double* D, int nD, int nbf) {
+  g_err.clear();
+  if (!D || nD < 1 || nbf < 1) return fail(ERI_ERR_ARG, "D is NULL or nD, nbf < 1");
+  double asym = 0.0, mx = 0.0;
+  for (int x = 0; x < nD; ++x) {
+    const double* Dx = D + (size_t)x * nbf * nbf;
+    for (int i = 0; i < nbf; ++i)
+      for (int j = 0; j < nbf; ++j) {
+        const double a = Dx[(size_t)i * nbf + j];
+        if (!std::isfinite(a)) return fail(ERI_ERR_ARG, "D has a non-finite element");
+        mx = std::max(mx, std::fabs(a));
+        if (j > i) asym = std::max(asym, std::fabs(a - Dx[(size_t)j * nbf + i]));
+      }
+  }
+  if (!(asym <= 1e-12 * mx))
+    return fail(ERI_ERR_ARG, "D is not symmetric: max|D_ij - D_ji| = %.3e, max|D| = %.3e", asym, mx);
   return ERI_OK;
 }
 
@@ -1698,7 +1793,34 @@ struct eri_batch {
   // its own half of the merged lists, tile counts, small counters and scratch
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_done = nullptr;             // end of the last call on its stream
+  bool called = false;
 };
+
+namespace {
+// Grow a batch buffer without synchronising the host or the device: the old buffer is freed
+// and the new one allocated in stream order on the call's stream, after the previous call's
+// work (ev_done); capacities grow by half again so that a growing job mix regrows rarely.
+template <typename T>
+eri_status ensure_batch_buf(eri_batch* b, T** ptr, size_t* cap, size_t n, cudaStream_t st) {
+  if (n <= *cap) return ERI_OK;
+  if (b->called) CUDA_TRY(cudaStreamWaitEvent(st, b->ev_done, 0));
+  if (*ptr) {
+    CUDA_TRY(cudaFreeAsync(*ptr, st));
+    *ptr = nullptr;
+    *cap = 0;
+  }
+  const size_t grow = std::max(n, n + n / 2);
+  cudaError_t e = cudaMallocAsync((void**)ptr, sizeof(T) * grow, st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *ptr = nullptr;
+    return fail(ERI_ERR_OOM, "stream-ordered allocation of %zu bytes failed", sizeof(T) * grow);
+  }
+  *cap = grow;
+  return ERI_OK;
+}
+}  // namespace
 
 extern "C" {
 
@@ -1737,6 +1859,7 @@ eri_status eri_batch_destroy(eri_batch* b) {
   if (b->side) cudaStreamDestroy(b->side);
   if (b->ev_fork) cudaEventDestroy(b->ev_fork);
   if (b->ev_join) cudaEventDestroy(b->ev_join);
+  if (b->ev_done) cudaEventDestroy(b->ev_done);
   delete b;
   return ERI_OK;
 }
@@ -1755,7 +1878,6 @@ eri_status eri_jk_batch(eri_batch* b, int njobs, eri_plan* const* plans, const d
   eri_plan* p0 = plans[0];
   // ---- job descriptors
   std::vector<JobDesc> jobs(njobs);
-  bool any_mixed = false;
   for (int j = 0; j < njobs; ++j) {
     eri_plan* p = plans[j];
     JobDesc& jd = jobs[j];
@@ -1773,16 +1895,25 @@ eri_status eri_jk_batch(eri_batch* b, int njobs, eri_plan* const* plans, const d
       jd.type_off[t] = p->type_off[t];
       jd.type_cnt[t] = p->type_cnt[t];
     }
-    any_mixed = any_mixed || p->opts.precision == ERI_MIXED;
   }
-  if ((s = ensure_buf(&b->d_jobs, &b->jobs_cap, (size_t)njobs)) != ERI_OK) return s;
+  if (!b->side) {
+    CUDA_TRY(cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking));
+    CUDA_TRY(cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming));
+    CUDA_TRY(cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming));
+    CUDA_TRY(cudaEventCreateWithFlags(&b->ev_done, cudaEventDisableTiming));
+  }
+  // the previous call's kernels may still read the job table and lists: this call's writes
+  // to them are ordered after that call's end
+  if (b->called) CUDA_TRY(cudaStreamWaitEvent(st, b->ev_done, 0));
+  if ((s = ensure_batch_buf(b, &b->d_jobs, &b->jobs_cap, (size_t)njobs, st)) != ERI_OK) return s;
   CUDA_TRY(cudaMemcpyAsync(b->d_jobs, jobs.data(), sizeof(JobDesc) * njobs, cudaMemcpyHostToDevice, st));
   // ---- classes present in any job, their merged capacities and launch shapes
-  struct BL { int X, Y; long long total; long long maxnt; };
+  struct BL { int X, Y; long long total; long long maxnt; int any_fp32; };
   std::vector<BL> cls;
   for (int X = 0; X < ERI_NPAIRTYPE; ++X)
     for (int Y = 0; Y <= X; ++Y) {
       long long tot = 0, mx = 0;
+      int any32 = 0;
       for (int j = 0; j < njobs; ++j) {
         const long long nx = plans[j]->type_cnt[X], ny = plans[j]->type_cnt[Y];
         if (!nx || !ny) continue;
@@ -1790,8 +1921,9 @@ eri_status eri_jk_batch(eri_batch* b, int njobs, eri_plan* const* plans, const d
         if ((unsigned long long)nt > 0xffffffffULL) return fail(ERI_ERR_ARG, "job %d has more than 2^32 tasks in a class", j);
         tot += nt;
         mx = std::max(mx, nt);
+        if (plans[j]->opts.precision == ERI_MIXED && fp32_pays(plans[j], X, Y, nt)) any32 = 1;
       }
-      if (tot) cls.push_back({X, Y, tot, mx});
+      if (tot) cls.push_back({X, Y, tot, mx, any32});
     }
   size_t cap = 1, tcap = 2, need = 0;
   struct LL { int X, Y, fp32, grid, smem, ts, small; long long total; };
@@ -1799,7 +1931,7 @@ eri_status eri_jk_batch(eri_batch* b, int njobs, eri_plan* const* plans, const d
   for (const BL& c : cls) {
     cap = std::max(cap, (size_t)c.total);
     tcap = std::max(tcap, (size_t)(2 * ((c.maxnt + 1023) / 1024 + 1)));
-    for (int fp32 = 0; fp32 < (any_mixed ? 2 : 1); ++fp32) {
+    for (int fp32 = 0; fp32 < (c.any_fp32 ? 2 : 1); ++fp32) {
       LL l{c.X, c.Y, fp32, 0, 0, 0, 0, c.total};
       if ((s = launch_shape(p0, c.X, c.Y, fp32, c.total, &l.grid, &l.smem, &l.ts)) != ERI_OK) return s;
       const ClassDesc& cd = p0->dev->classes[c.X][c.Y];
@@ -1818,23 +1950,16 @@ eri_status eri_jk_batch(eri_batch* b, int njobs, eri_plan* const* plans, const d
   cap = (cap + 31) & ~(size_t)31;
   tcap = (tcap + 31) & ~(size_t)31;
   need = (need + 31) & ~(size_t)31;
-  if ((s = ensure_buf(&b->d_blist, &b->blist_cap, 2 * cap)) != ERI_OK) return s;
-  if ((s = ensure_buf(&b->d_tiles, &b->tiles_cap, 2 * tcap)) != ERI_OK) return s;
-  if (2 * need > b->scratch_doubles) {
-    if (b->d_scratch) {
-      CUDA_TRY(cudaDeviceSynchronize());
-      cudaFree(b->d_scratch);
-      b->d_scratch = nullptr;
-      b->scratch_doubles = 0;
-    }
-    CUDA_TRY(cudaMalloc(&b->d_scratch, sizeof(double) * 2 * need));
-    b->scratch_doubles = 2 * need;
-  }
-  if (!b->side) {
-    CUDA_TRY(cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking));
-    CUDA_TRY(cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming));
-    CUDA_TRY(cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming));
-  }
+  // per-stream halves sized from the largest request seen; when they grow they are
+  // reallocated with stream-ordered frees and allocations (no host or device synchronisation)
+  if (cap > b->blist_cap / 2 && (s = ensure_batch_buf(b, &b->d_blist, &b->blist_cap, 2 * cap, st)) != ERI_OK) return s;
+  if (tcap > b->tiles_cap / 2 && (s = ensure_batch_buf(b, &b->d_tiles, &b->tiles_cap, 2 * tcap, st)) != ERI_OK) return s;
+  if (need > b->scratch_doubles / 2 &&
+      (s = ensure_batch_buf(b, &b->d_scratch, &b->scratch_doubles, 2 * need, st)) != ERI_OK)
+    return s;
+  cap = b->blist_cap / 2;
+  tcap = b->tiles_cap / 2;
+  need = b->scratch_doubles / 2;
   const cudaStream_t ss[2] = {st, b->side};
   // ---- per job: zero outputs, density block maxima
   for (int j = 0; j < njobs; ++j) {
@@ -1876,9 +2001,9 @@ eri_status eri_jk_batch(eri_batch* b, int njobs, eri_plan* const* plans, const d
       a.nsh = p->nshell;
       a.tau = p->opts.screen_thresh;
       a.mixed_thr = p->opts.mixed_thresh;
+      const bool split = p->opts.precision == ERI_MIXED && fp32_pays(p, c.X, c.Y, a.ntask);
       CUDA_TRY(erik_launch_compact_batched(&a, blist_l, (unsigned long long)c.total, small_l, tiles_l, cursor,
-                                           small_l + 2, (unsigned long long)j,
-                                           p->opts.precision == ERI_MIXED ? 1 : 0, sl));
+                                           small_l + 2, (unsigned long long)j, split ? 1 : 0, sl));
     }
     for (const LL& l : launches) {
       if (l.X != c.X || l.Y != c.Y) continue;
@@ -1907,6 +2032,8 @@ eri_status eri_jk_batch(eri_batch* b, int njobs, eri_plan* const* plans, const d
     if (flags[j] & 1) CUDA_TRY(erik_launch_symmetrize(J[j], nD[j], plans[j]->nbf, st));
     if (flags[j] & 2) CUDA_TRY(erik_launch_symmetrize(K[j], nD[j], plans[j]->nbf, st));
   }
+  CUDA_TRY(cudaEventRecord(b->ev_done, st));
+  b->called = true;
   b->last_stream = st;
   b->last_launches = li;
   return ERI_OK;

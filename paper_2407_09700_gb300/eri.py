@@ -39,7 +39,8 @@ class eri_basis(ctypes.Structure):
 
 class eri_opts(ctypes.Structure):
     _fields_ = [("screen_thresh", ctypes.c_double), ("precision", ctypes.c_int),
-                ("mixed_thresh", ctypes.c_double), ("max_nd", ctypes.c_int)]
+                ("mixed_thresh", ctypes.c_double), ("max_nd", ctypes.c_int), ("mixed_min_tasks", ctypes.c_int),
+                ("check_symmetric", ctypes.c_int)]
 
 
 class eri_stats(ctypes.Structure):
@@ -47,7 +48,7 @@ class eri_stats(ctypes.Structure):
                 ("prim_quartets", ctypes.c_longlong), ("quartets_fp32", ctypes.c_longlong),
                 ("model_flops", ctypes.c_double), ("npairs_total", ctypes.c_int),
                 ("npairs_kept", ctypes.c_int), ("nclasses_launched", ctypes.c_int),
-                ("model_flops_fp32", ctypes.c_double)]
+                ("model_flops_fp32", ctypes.c_double), ("device_status", ctypes.c_int)]
 
 
 class eri_launch_record(ctypes.Structure):
@@ -75,6 +76,7 @@ _SIGS = {
     "eri_grad_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong),
                                       ctypes.POINTER(ctypes.c_longlong)]),
     "eri_shell_quartet": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int] * 4 + [_dp]),
+    "eri_check_density": (ctypes.c_int, [_dp, ctypes.c_int, ctypes.c_int]),
     "eri_schwarz": (ctypes.c_int, [ctypes.c_void_p, _dp]),
     "eri_schwarz_transfer": (ctypes.c_int, [ctypes.c_void_p, _dp]),
     "eri_rys_roots": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp]),
@@ -145,7 +147,7 @@ class Plan:
     """An eri_plan built from a molecule-like object (coords, shell_* arrays, exps, coefs)."""
 
     def __init__(self, mol, tau=None, precision=ERI_FP64, mixed_thresh=1e-4, max_nd=8, normalise=True,
-                 stream=None):
+                 stream=None, check_symmetric=False, mixed_min_tasks=65536):
         lib = load_library()
         self._arrs = dict(
             coords=np.ascontiguousarray(mol.coords, dtype=np.float64),
@@ -163,7 +165,8 @@ class Plan:
                       _i(A["nprim"]), _i(A["off"]), _d(A["exps"]), _d(A["coefs"]), 1 if normalise else 0)
         if tau is None:
             tau = getattr(mol, "tau", 1e-12)
-        o = eri_opts(float(tau), int(precision), float(mixed_thresh), int(max_nd))
+        o = eri_opts(float(tau), int(precision), float(mixed_thresh), int(max_nd), int(mixed_min_tasks),
+                     1 if check_symmetric else 0)
         h = ctypes.c_void_p()
         st = ctypes.c_void_p(0) if stream is None else _stream_handle(stream)
         _check(lib.eri_plan_create(ctypes.byref(b), ctypes.byref(o), st, ctypes.byref(h)))
@@ -266,6 +269,15 @@ class Plan:
         s = eri_stats()
         _check(load_library().eri_flop_stats(self._h, ctypes.byref(s)))
         return {k: getattr(s, k) for k, _ in eri_stats._fields_}
+
+
+def check_density(D):
+    """Raise EriError (ERI_ERR_ARG) unless every density of D [nD, nbf, nbf] (or [nbf, nbf],
+    host array) is symmetric to 1e-12 of its largest element; needs no GPU."""
+    D = np.ascontiguousarray(D, dtype=np.float64)
+    if D.ndim == 2:
+        D = D[None]
+    _check(load_library().eri_check_density(_d(D), int(D.shape[0]), int(D.shape[1])))
 
 
 def rys_roots(N, T):

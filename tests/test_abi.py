@@ -47,6 +47,8 @@ def test_argument_validation_before_device(lib):
     assert _create(lib, b, E.eri_opts(-1.0, 0, 1e-4, 1)) == E.ERI_ERR_ARG
     assert _create(lib, b, E.eri_opts(1e-12, 0, 1e-4, 0)) == E.ERI_ERR_ARG
     assert _create(lib, b, E.eri_opts(1e-12, 7, 1e-4, 1)) == E.ERI_ERR_ARG
+    assert _create(lib, b, E.eri_opts(1e-12, 0, 1e-4, 1, 0, 2)) == E.ERI_ERR_ARG
+    assert _create(lib, b, E.eri_opts(1e-12, 0, 1e-4, 1, -1, 0)) == E.ERI_ERR_ARG
     keep["l"][2] = 5
     assert _create(lib, b, good) == E.ERI_ERR_UNSUPPORTED_L
     assert b"l = 5" in lib.eri_last_error()
@@ -109,3 +111,27 @@ def test_binding_declares_every_header_symbol(lib):
     only: no entry point is reached without argtypes)."""
     missing = [n for n in pkg.header_symbols() if n not in E._SIGS]
     assert not missing, missing
+
+
+def test_density_symmetry_check_on_host(lib):
+    """eri_check_density (the check_symmetric option's host test; Sec. 3's 8-fold symmetry
+    needs a symmetric D): a symmetric density passes, one perturbed above 1e-12 of max|D|
+    is rejected with ERI_ERR_ARG, a non-finite element too; no GPU needed."""
+    rng = np.random.default_rng(4)
+    C = rng.normal(size=(2, 12, 5))
+    D = np.einsum("xik,xjk->xij", C, C)
+    pkg.check_density(D)
+    pkg.check_density(D[0])
+    bad = D.copy()
+    bad[1, 3, 7] += 1e-9 * np.abs(D).max()
+    with pytest.raises(pkg.EriError) as ei:
+        pkg.check_density(bad)
+    assert ei.value.status == E.ERI_ERR_ARG and "not symmetric" in str(ei.value)
+    tiny = D.copy()
+    tiny[0, 2, 5] += 1e-14 * np.abs(D).max()
+    pkg.check_density(tiny)
+    nan = D.copy()
+    nan[0, 1, 1] = float("nan")
+    with pytest.raises(pkg.EriError):
+        pkg.check_density(nan)
+    assert lib.eri_check_density(None, 1, 3) == E.ERI_ERR_ARG
