@@ -11,8 +11,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liberi.so")
-SOURCES = ["eri_kernels.cu", "eri_small.cu", "eri_grad.cu", "eri_plan.cpp", "rys_table.cpp", "eri_noalloc.cu", "eri_onee.cpp"]
-HEADERS = ["eri_internal.h", "rys_table.h", "eri_device.cuh", os.path.join("..", "..", "include", "eri.h")]
+SOURCES = ["eri_kernels.cu", "eri_class_spec.cu", "eri_small.cu", "eri_grad.cu", "eri_plan.cpp", "rys_table.cpp",
+           "eri_noalloc.cu", "eri_onee.cpp"]
+HEADERS = ["eri_internal.h", "rys_table.h", "eri_device.cuh", "eri_class_kernel.cuh",
+           os.path.join("..", "..", "include", "eri.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1,17 +1,17 @@
 // eri_jk_noalloc: the J/K build of eri_jk for callers that must not allocate device memory
 // during the call, with the class kernels' team scratch taken from a fixed static array.
 //
-// Why: eri_jk grows the plan's scratch buffer with cudaMalloc (after a device-wide
-// synchronisation) the first time a larger class is launched.  Code running inside CUDA
-// stream capture, inside a host callback, or under an external allocator that owns the
-// device's memory cannot let a library call cudaMalloc / cudaFree at that point.  This
-// entry point calls neither, nor any allocating library routine.
+// Why: the plan's scratch buffer is shared with eri_jk_grad and eri_shell_quartet, which
+// may regrow it with cudaMalloc / cudaFree after a device-wide synchronisation.  Code
+// running under an allocator or a memory budget that owns the device's memory, or inside
+// a host callback, cannot let a library call cudaMalloc / cudaFree.  This entry point calls
+// neither, nor any allocating library routine.
 //
 // The scratch lives in g_noalloc_scratch below: ERI_NOALLOC_SCRATCH_BYTES (32 MiB) of
 // device memory that every GPU loading this library holds until the process exits.  Host
 // code cannot use the array's name as a device address (on the host it is only a
 // stand-in), so the address is looked up once per device with cudaGetSymbolAddress and
-// cached.
+// cached (for the life of the process: it is not looked up again after a device reset).
 #include <cuda_runtime.h>
 
 #include <mutex>

@@ -160,10 +160,25 @@ def test_jk_high_l_reduced():
 
 # ---------------------------------------------------------------- mixed precision (FP32 recurrences)
 
-def _expected_split(m, Q, Qe, tau, thr):
+def _pair_type(l0, l1):
+    a, b = max(l0, l1), min(l0, l1)
+    return a * (a + 1) // 2 + b, (a, b)
+
+
+def _fp32_classes(plan, D):
+    """Classes (la, lb, lc, ld) that ran an FP32 launch in a profiled build of D."""
+    plan.set_profiling(True)
+    plan.jk(torch.from_numpy(np.ascontiguousarray(D)).cuda())
+    recs = plan.launch_records()
+    plan.set_profiling(False)
+    return {(r["la"], r["lb"], r["lc"], r["ld"]) for r in recs if r["fp32"]}
+
+
+def _expected_split(m, Q, Qe, tau, thr, fp32_classes=None):
     """Unique shell quartets passing the screen Q_ij * Q_kl * max|D| >= tau (six cross blocks),
-    split by the mixed mode's bound Qe_ij * Qe_kl * max|D| > thr (FP64) or <= thr (FP32),
-    evaluated in the kernel's order of operations."""
+    split by the mixed mode's bound Qe_ij * Qe_kl * max|D| > thr (FP64) or <= thr (FP32) in
+    the classes that run an FP32 launch (every quartet of the others is FP64), evaluated in
+    the kernel's order of operations."""
     f0 = m.shell_first_bf()
     ns = m.nshell
     nf = [(int(l) + 1) * (int(l) + 2) // 2 for l in m.shell_l]
@@ -179,10 +194,14 @@ def _expected_split(m, Q, Qe, tau, thr):
             R, S = pairs[b]
             dm = max(max(Dmax[P, Qs], Dmax[R, S]), max(max(Dmax[P, R], Dmax[P, S]), max(Dmax[Qs, R], Dmax[Qs, S])))
             if Q[P, Qs] * Q[R, S] * dm >= tau:
-                if Qe[P, Qs] * Qe[R, S] * dm > thr:
-                    n64 += 1
-                else:
+                tx, cx = _pair_type(int(m.shell_l[P]), int(m.shell_l[Qs]))
+                ty, cy = _pair_type(int(m.shell_l[R]), int(m.shell_l[S]))
+                cls = cx + cy if tx >= ty else cy + cx
+                split = fp32_classes is None or cls in fp32_classes
+                if split and not (Qe[P, Qs] * Qe[R, S] * dm > thr):
                     n32 += 1
+                else:
+                    n64 += 1
     return n64, n32
 
 
@@ -194,11 +213,12 @@ MIXED_THRESH = 1e-4      # the split of the mixed mode: FP64 above a bound of 1e
                                              (lambda: config_high_l(seed=6, natm=2, nocc=20), False)])
 def test_jk_mixed_precision_within_1e6(make, some_fp32):
     m = make()
-    plan = pkg.Plan(m, precision=pkg.ERI_MIXED, mixed_thresh=MIXED_THRESH)
+    plan = pkg.Plan(m, precision=pkg.ERI_MIXED, mixed_thresh=MIXED_THRESH, mixed_min_tasks=0)
+    cls32 = _fp32_classes(plan, m.D)
     J, K = _jk_gpu(plan, m.D)
     Jr, Kr, n = oracle.jk(m)
     st = plan.stats()
-    n64, n32 = _expected_split(m, plan.schwarz(), plan.schwarz_transfer(), m.tau, MIXED_THRESH)
+    n64, n32 = _expected_split(m, plan.schwarz(), plan.schwarz_transfer(), m.tau, MIXED_THRESH, cls32)
     assert st["quartets_computed"] == n64 + n32
     assert st["quartets_fp32"] == n32
     assert n32 > 0 or not some_fp32
@@ -252,7 +272,7 @@ def test_mixed_threshold_extremes():
     assert p0.stats()["quartets_fp32"] == 0
     assert np.abs(J - Jr).max() <= 1e-10 and np.abs(K - Kr).max() <= 1e-10
     # threshold huge: everything runs in FP32; still close to the FP64 result
-    p1 = pkg.Plan(m, precision=pkg.ERI_MIXED, mixed_thresh=1e30)
+    p1 = pkg.Plan(m, precision=pkg.ERI_MIXED, mixed_thresh=1e30, mixed_min_tasks=0)
     J, K = _jk_gpu(p1, m.D)
     assert p1.stats()["quartets_fp32"] == n
     assert np.abs(J - Jr).max() <= 1e-5 and np.abs(K - Kr).max() <= 1e-5
@@ -302,9 +322,10 @@ D = random_psd_density(m.nbf, 6, rng)
 np.save(sys.argv[1], D)
 out = {}
 for name, prec in (("fp64", pkg.ERI_FP64), ("mixed", pkg.ERI_MIXED)):
-    plan = pkg.Plan(m, tau=0.0, precision=prec, mixed_thresh=1e-2)
+    plan = pkg.Plan(m, tau=0.0, precision=prec, mixed_thresh=1e-2, mixed_min_tasks=0)
     J, K = plan.jk(torch.from_numpy(D).cuda())
     torch.cuda.synchronize()
+    assert plan.stats()["device_status"] == 0
     out[name] = [J.cpu().numpy().tolist(), K.cpu().numpy().tolist()]
     plan.close()
 print(json.dumps(out))
@@ -318,6 +339,8 @@ print(json.dumps(out))
     # the same classes at 8 and 32 lanes with lane programs only
     "1 1 1 1 32 0;2 0 1 1 8 0;2 0 2 0 32 0;2 1 1 0 8 0;2 1 1 1 32 0;2 1 2 0 8 0;2 1 2 1 32 0;2 2 1 0 8 0;"
     "2 2 1 1 8 0;2 2 2 0 32 0;2 2 2 1 32 0;2 2 2 2 32 0",
+    # (dp|dp) with its pair records staged into shared memory by bulk copies, both assembly paths
+    "2 1 2 1 8 1 1", "2 1 2 1 8 0 1",
 ])
 def test_jk_team_size_overrides(tmp_path, cfg):
     """The tuning override changes team sizes and the assembly path, never the result:
@@ -404,3 +427,41 @@ def test_jk_full_size_sampled_blocks(name, precision, tol):
     _check_blocks(m, pairs, Jl, Kl, J, K, tol)
     st = plan.stats()
     assert st["quartets_computed"] > 0
+
+
+def test_check_symmetric_option_rejects_asymmetric_density():
+    """With check_symmetric the build verifies Sec. 3's precondition (symmetric D, needed by
+    the 8-fold symmetry) on the device and on the host path, and returns ERI_ERR_ARG."""
+    m = config_tiny(seed=4)
+    plan = pkg.Plan(m, check_symmetric=True)
+    D = torch.from_numpy(m.D).cuda()
+    J, K = _jk_gpu(plan, m.D)
+    Jr, Kr, _ = oracle.jk(m)
+    assert np.abs(J - Jr).max() <= 1e-10
+    bad = m.D.copy()
+    bad[0, 2, 9] += 1e-6
+    with pytest.raises(pkg.EriError) as ei:
+        plan.jk(torch.from_numpy(bad).cuda())
+    assert ei.value.status == pkg.eri.ERI_ERR_ARG and "not symmetric" in str(ei.value)
+    with pytest.raises(pkg.EriError):
+        plan.jk_host(bad)
+    plain = pkg.Plan(m)             # without the option an asymmetric D is not checked
+    plain.jk(torch.from_numpy(bad).cuda())
+    torch.cuda.synchronize()
+
+
+def test_mixed_min_tasks_and_fp32_classes():
+    """A class gets its FP32 launch only when its task space reaches mixed_min_tasks; a
+    large mixed_min_tasks gives the FP64 result and no FP32 quartet, 0 an FP32 launch for
+    every class."""
+    m = _mixed_molecule(seed=3, spread=4.0)
+    big = pkg.Plan(m, precision=pkg.ERI_MIXED, mixed_thresh=1e30, mixed_min_tasks=1 << 30)
+    J, K = _jk_gpu(big, m.D)
+    Jr, Kr, _ = oracle.jk(m)
+    assert big.stats()["quartets_fp32"] == 0
+    assert np.abs(J - Jr).max() <= 1e-10 and np.abs(K - Kr).max() <= 1e-10
+    allp = pkg.Plan(m, precision=pkg.ERI_MIXED, mixed_thresh=1e30, mixed_min_tasks=0)
+    cls32 = _fp32_classes(allp, m.D)
+    assert (1, 0, 0, 0) in cls32 and (1, 1, 1, 1) in cls32 and (4, 4, 4, 4) in cls32
+    J, K = _jk_gpu(allp, m.D)        # every quartet FP32, up to (gg|gg): close, not 1e-6
+    assert np.abs(J - Jr).max() <= 1e-3 * np.abs(Jr).max() and np.abs(K - Kr).max() <= 1e-3 * np.abs(Kr).max()

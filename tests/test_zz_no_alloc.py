@@ -1,7 +1,9 @@
 """eri_jk_noalloc: the J/K build for callers that cannot allocate device memory during
-the call (inside CUDA stream capture, in a host callback, or under an allocator that
-owns the device memory).  It must give the same J and K as eri_jk, call after call,
-while the device's free memory stays unchanged.
+the call (code running under an allocator or a memory budget that owns the device's
+memory, or in a host callback, where a library's cudaMalloc / cudaFree is not allowed).
+It must give the same J and K as eri_jk, call after call, while the device's free memory
+stays unchanged; in the mixed mode its FP32 launches (which read no task list) must also
+stay within the mixed mode's 1e-6 of the oracle.
 
 Kept in its own file, collected last, so a run that stops at the first failure has
 already run every other test.
@@ -16,6 +18,7 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
+import oracle  # noqa: E402
 import paper_2407_09700_gb300 as pkg  # noqa: E402
 from workloads import config_high_l, config_tiny, custom_molecule, random_psd_density  # noqa: E402
 
@@ -49,11 +52,15 @@ def _mixed(seed):
     return m
 
 
-@pytest.mark.parametrize("make", [lambda: config_tiny(seed=2), lambda: _mixed(7),
-                                  lambda: config_high_l(seed=1, natm=2, nocc=20)])
-def test_noalloc_matches_eri_jk_twice(lib, make):
+@pytest.mark.parametrize("make,precision", [(lambda: config_tiny(seed=2), pkg.ERI_FP64),
+                                            (lambda: _mixed(7), pkg.ERI_FP64),
+                                            (lambda: config_high_l(seed=1, natm=2, nocc=20), pkg.ERI_FP64),
+                                            (lambda: _mixed(7), pkg.ERI_MIXED),
+                                            (lambda: config_high_l(seed=1, natm=3, nocc=20), pkg.ERI_MIXED)])
+def test_noalloc_matches_eri_jk_twice(lib, make, precision):
     m = make()
-    plan = pkg.Plan(m)
+    # mixed: split 1e-2 and no minimum class size, so FP32 launches (reading no task list) run
+    plan = pkg.Plan(m, precision=precision, mixed_thresh=1e-2, mixed_min_tasks=0)
     D = torch.from_numpy(m.D).cuda()
     Jref, Kref = plan.jk(D)
     torch.cuda.synchronize()
@@ -71,6 +78,12 @@ def test_noalloc_matches_eri_jk_twice(lib, make):
         dj = float(np.abs(J.cpu().numpy() - Jref).max())
         dk = float(np.abs(K.cpu().numpy() - Kref).max())
         assert dj <= TOL and dk <= TOL, (call, dj, dk)
+    if precision == pkg.ERI_MIXED:
+        st = plan.stats()
+        assert st["quartets_fp32"] > 0
+        Jo, Ko, _ = oracle.jk(m)
+        assert float(np.abs(J.cpu().numpy() - Jo).max()) <= 1e-6
+        assert float(np.abs(K.cpu().numpy() - Ko).max()) <= 1e-6
     plan.close()
 
 
