@@ -10,7 +10,10 @@ library's host routine (the paper also computes them on the CPU, Sec. 4).
 
 Conventions (the paper does not print PySCF's): core-Hamiltonian guess,
 canonical orthogonalisation dropping overlap eigenvalues below 1e-8, DIIS with 8
-vectors starting at the second iteration.
+vectors starting at the second iteration.  With incremental = True (PySCF's direct-SCF
+scheme, on which the paper's GPU4PySCF builds) every build after the first evaluates J
+and K of the density change D_n - D_{n-1} and adds them to the previous J and K; the
+screening of Eqs. 7-9 then uses max|D_n - D_{n-1}|, which shrinks as the SCF converges.
 """
 
 from __future__ import annotations
@@ -46,14 +49,16 @@ class SCFResult:
 
 
 class RHF:
-    def __init__(self, mol, charge: Optional[int] = None, precision: int = ERI_FP64, mixed_thresh: float = 1e-5,
+    def __init__(self, mol, charge: Optional[int] = None, precision: int = ERI_FP64, mixed_thresh: float = 1e-4,
                  tau: Optional[float] = None, lindep: float = 1e-8, plan: Optional[Plan] = None, stream=None,
-                 device: str = "cuda"):
+                 device: str = "cuda", incremental: bool = False):
         """device: where the matrices live ("cuda"; the step-wise start / update interface also
-        runs on "cpu" with J and K supplied by the caller)."""
+        runs on "cpu" with J and K supplied by the caller).  incremental: build J, K of the
+        density change after the first iteration (see the module docstring)."""
         import torch
         self.torch = torch
         self.mol = mol
+        self.incremental = bool(incremental)
         if charge is None:
             charge = int(getattr(mol, "net_charge", 0))
         nel = int(round(float(np.sum(mol.charges)))) - charge
@@ -88,40 +93,58 @@ class RHF:
         self.fs, self.es, self.energies = [], [], []
         self.e_old = None
         self.converged = False
+        self.J_acc = self.K_acc = self.D_acc = None
         if D0 is None:
             self.D, self.mo_e = self._density(self.H)
         else:
             self.D, self.mo_e = D0, None
         return self.D
 
+    def build_density(self):
+        """The density whose J and K the next update() expects: D, or with incremental builds
+        (after the first) the change D - D_prev since the last build."""
+        if self.incremental and self.D_acc is not None:
+            return self.D - self.D_acc
+        return self.D
+
     def update(self, J, K, conv_tol: Optional[float] = 1e-8):
-        """One SCF step from J, K of the current density: Fock matrix, energy, DIIS, new density.
-        Returns (energy, converged)."""
+        """One SCF step from J, K of build_density(): Fock matrix, energy, DIIS, new density.
+        Returns (energy, converged).  The energy is read back to the host once per step (the
+        convergence test); DIIS runs on the device."""
         torch = self.torch
         D = self.D
+        if self.incremental and self.D_acc is not None:
+            J = self.J_acc + J
+            K = self.K_acc + K
+        if self.incremental:
+            self.J_acc, self.K_acc, self.D_acc = J, K, D
         F = self.H + J - 0.5 * K
-        energy = float(0.5 * torch.sum(D * (self.H + F))) + self.enuc
-        self.energies.append(energy)
+        e_dev = 0.5 * torch.sum(D * (self.H + F))
         err = self.X.T @ (F @ D @ self.S - self.S @ D @ F) @ self.X
         self.fs.append(F)
         self.es.append(err)
         if len(self.fs) > self.diis_space:
             self.fs.pop(0)
             self.es.pop(0)
-        if len(self.fs) >= 2 and float(err.abs().max()) > 1e-13:
+        if len(self.fs) >= 2:
+            # B_ij = <e_i, e_j> for all stored error vectors at once; the extrapolation is skipped
+            # (coefficients of the newest Fock matrix) once the error is below 1e-13
             n = len(self.fs)
-            B = torch.empty((n + 1, n + 1), dtype=torch.float64, device=F.device)
-            for i in range(n):
-                for j in range(i + 1):
-                    B[i, j] = B[j, i] = torch.sum(self.es[i] * self.es[j])
-            B[n, :] = -1.0
-            B[:, n] = -1.0
+            E = torch.stack([e.reshape(-1) for e in self.es])
+            B = torch.full((n + 1, n + 1), -1.0, dtype=torch.float64, device=F.device)
+            B[:n, :n] = E @ E.T
             B[n, n] = 0.0
             rhs = torch.zeros(n + 1, dtype=torch.float64, device=F.device)
             rhs[n] = -1.0
-            c = torch.linalg.solve(B, rhs)
-            F = sum(c[i] * self.fs[i] for i in range(n))
+            sol, info = torch.linalg.solve_ex(B, rhs)
+            last = torch.zeros(n, dtype=torch.float64, device=F.device)
+            last[n - 1] = 1.0
+            use = (err.abs().max() > 1e-13) & (info == 0) & torch.isfinite(sol).all()
+            c = torch.where(use, torch.nan_to_num(sol[:n]), last)
+            F = torch.einsum("i,ijk->jk", c, torch.stack(self.fs))
         self.D, self.mo_e = self._density(F)
+        energy = float(e_dev) + self.enuc
+        self.energies.append(energy)
         if conv_tol is not None and self.e_old is not None and abs(energy - self.e_old) < conv_tol:
             self.converged = True
         self.e_old = energy
@@ -141,9 +164,11 @@ class RHF:
         for it in range(1, n_iter + 1):
             ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             ev0.record()
-            self.plan.jk(self.D.unsqueeze(0).contiguous(), J, K, stream=self.stream)
+            self.plan.jk(self.build_density().unsqueeze(0).contiguous(), J, K, stream=self.stream)
             ev1.record()
-            _, conv = self.update(J[0], K[0], conv_tol if fixed_iters is None else None)
+            _, conv = self.update(J[0].clone() if self.incremental else J[0],
+                                  K[0].clone() if self.incremental else K[0],
+                                  conv_tol if fixed_iters is None else None)
             jk_t.append(ev0.elapsed_time(ev1) / 1e3)
             if conv:
                 break
@@ -168,7 +193,7 @@ def main():
     ap.add_argument("--natm", type=int, default=120)
     ap.add_argument("--iters", type=int, default=20)
     ap.add_argument("--seed", type=int, default=0)
-    ap.add_argument("--mixed-thresh", type=float, default=1e-5)
+    ap.add_argument("--mixed-thresh", type=float, default=1e-4)
     args = ap.parse_args()
     build()
     mol = config_scf(seed=args.seed, natm=args.natm)

@@ -12,16 +12,23 @@ convergence threshold) arrive over time.  The server
     the pending J/K build of every active job, with each angular-momentum class
     run as one launch over all jobs (the class kernels read each task's plan,
     D, J and K from a job table), then each job takes its own step (J/K jobs
-    finish, RHF jobs update F, E, DIIS and D);
+    finish, RHF jobs update F, E, DIIS and D; RHF jobs build J and K of the
+    density change after their first iteration, as PySCF's direct SCF does);
+  * builds the plans (pair data, Schwarz factors) and RHF set-up of arrived
+    requests ahead of admission on a worker thread with its own CUDA stream, so
+    that plan creation does not hold up the tick, and frees retired jobs' plans
+    only when no job is active or an admission needs the memory (freeing device
+    memory waits for the whole device);
   * records arrival, admission and finish times, giving throughput and
     p50 / p99 latency (finish - arrival).
 
 ``run_sequential`` is the baseline: the same requests one at a time, in arrival
-order, each with its own FP64 plan.
+order, each with its own FP64 plan (RHF jobs with the same incremental builds).
 """
 
 from __future__ import annotations
 
+import concurrent.futures
 import dataclasses
 import math
 import time
@@ -49,6 +56,8 @@ class Job:
     finish: float = math.nan
     iters: int = 0
     result: Dict = dataclasses.field(default_factory=dict)
+    prepared: object = None       # future of the worker thread's preparation (plan, RHF set-up)
+    ready: object = None          # CUDA event after the preparation's device work
 
 
 def footprint_bytes(mol, kind: str) -> int:
@@ -69,10 +78,12 @@ def _percentile(x, q):
 
 class Server:
     def __init__(self, precision: int = ERI_MIXED, mixed_thresh: float = 1e-4, hbm_budget: int = 8 << 30,
-                 max_slots: int = 32, scf_conv: float = 1e-8, scf_max_iter: int = 100, batch=None, sync=None):
+                 max_slots: int = 32, scf_conv: float = 1e-8, scf_max_iter: int = 100, batch=None, sync=None,
+                 prefetch: int = 4):
         """batch: the batched J/K engine (an eri_batch by default); sync: waits for the device
         (torch.cuda.synchronize by default).  Both are replaceable so that the admission and
-        retirement policy can run against stand-ins."""
+        retirement policy can run against stand-ins.  prefetch: arrived requests whose plans
+        are built ahead of admission (0: build at admission)."""
         import torch
         self.torch = torch
         self.precision = precision
@@ -83,18 +94,43 @@ class Server:
         self.scf_max_iter = scf_max_iter
         self.batch = batch if batch is not None else Batch()
         self.sync = sync if sync is not None else torch.cuda.synchronize
+        self.prefetch = int(prefetch)
+        self.pool = concurrent.futures.ThreadPoolExecutor(1) if self.prefetch > 0 else None
+        self.prep_stream = None
         self.ticks = 0
         self.batch_sizes: List[int] = []
         self.max_active = 0
         self.max_used = 0
+        self.prepared_ahead = 0
+        self.freed_deferred = 0
+
+    # ---- preparation (worker thread): everything that does not need the job's turn
+    def _prepare(self, job: Job):
+        torch = self.torch
+        if self.prep_stream is None:
+            self.prep_stream = torch.cuda.Stream()
+        with torch.cuda.stream(self.prep_stream):
+            job.plan = Plan(job.mol, precision=self.precision, mixed_thresh=self.mixed_thresh,
+                            stream=self.prep_stream)
+            if job.kind == "scf":
+                job.scf = RHF(job.mol, plan=job.plan, incremental=True)
+            ev = torch.cuda.Event()
+            ev.record(self.prep_stream)
+            job.ready = ev
 
     def _admit(self, job: Job, now: float):
         torch = self.torch
-        job.plan = Plan(job.mol, precision=self.precision, mixed_thresh=self.mixed_thresh)
+        if job.prepared is not None:
+            job.prepared.result()
+            torch.cuda.current_stream().wait_event(job.ready)
+        else:
+            job.plan = Plan(job.mol, precision=self.precision, mixed_thresh=self.mixed_thresh)
+            if job.kind == "scf":
+                job.scf = RHF(job.mol, plan=job.plan, incremental=True)
         nbf = job.plan.nbf
         if job.kind == "scf":
-            job.scf = RHF(job.mol, plan=job.plan)
-            job.D = job.scf.start().unsqueeze(0).contiguous()
+            job.scf.start()
+            job.D = job.scf.build_density().unsqueeze(0).contiguous()
         else:
             job.D = torch.from_numpy(np.ascontiguousarray(job.mol.D[:1])).cuda()
         job.J = torch.empty((1, nbf, nbf), dtype=torch.float64, device="cuda")
@@ -103,36 +139,79 @@ class Server:
 
     def _retire(self, job: Job, now: float):
         job.finish = now
-        job.plan.close()
-        job.plan = None
         if job.scf is not None:
             job.scf.plan = None
             job.scf = None
         job.D = job.J = job.K = None
 
+    def _destroy(self, job: Job):
+        """Free a retired job's plan (synchronises the device)."""
+        if job.plan is not None:
+            job.plan.close()
+            job.plan = None
+
     def run(self, jobs: List[Job], keep_results: bool = False):
         """Serve jobs (sorted by arrival).  Wall-clock times are relative to the start."""
-        torch = self.torch
         pending = sorted(jobs, key=lambda j: j.arrival)
         active: List[Job] = []
-        used = 0
+        retired: List[Job] = []       # plans still held (freed when idle or when memory is needed)
+        used = 0                      # footprints of active, prepared and not yet freed jobs
         t0 = time.perf_counter()
+
+        def free_retired():
+            nonlocal used
+            for j in retired:
+                self._destroy(j)
+                used -= j.footprint
+                self.freed_deferred += 1
+            retired.clear()
+
         while pending or active:
             now = time.perf_counter() - t0
-            # ---- continuous admission: arrived, a slot free and the footprint fits
-            while (pending and pending[0].arrival <= now and len(active) < self.max_slots
-                   and used + pending[0].footprint <= self.hbm_budget):
-                j = pending.pop(0)
+            # ---- prepare arrived requests ahead of admission while the budget allows (their
+            #      footprint is counted from then on)
+            if self.pool is not None:
+                n_prep = sum(1 for j in pending if j.prepared is not None)
+                for j in pending:
+                    if n_prep >= self.prefetch or j.arrival > now:
+                        break
+                    if j.prepared is None:
+                        if used + j.footprint > self.hbm_budget:
+                            break
+                        j.prepared = self.pool.submit(self._prepare, j)
+                        used += j.footprint
+                        n_prep += 1
+                        self.prepared_ahead += 1
+                        self.max_used = max(self.max_used, used)
+            # ---- continuous admission: arrived and a slot free; a prepared job joins once its
+            #      preparation is done (waited for only when nothing else can run), otherwise the
+            #      footprint must fit
+            while pending and pending[0].arrival <= now and len(active) < self.max_slots:
+                j = pending[0]
+                if j.prepared is not None:
+                    if not j.prepared.done() and active:
+                        break
+                    extra = 0
+                else:
+                    extra = j.footprint
+                    if used + extra > self.hbm_budget:
+                        if retired:
+                            free_retired()
+                            continue
+                        break
+                pending.pop(0)
                 self._admit(j, now)
                 active.append(j)
-                used += j.footprint
+                used += extra
                 self.max_active = max(self.max_active, len(active))
                 self.max_used = max(self.max_used, used)
             if not active:
+                free_retired()
                 if pending:
                     if pending[0].footprint > self.hbm_budget:
                         raise RuntimeError(f"request {pending[0].rid} exceeds the HBM budget on its own")
-                    time.sleep(max(0.0, pending[0].arrival - (time.perf_counter() - t0)))
+                    if pending[0].arrival > time.perf_counter() - t0:
+                        time.sleep(max(0.0, min(pending[0].arrival - (time.perf_counter() - t0), 0.005)))
                 continue
             # ---- one batched J/K over every active job
             self.batch.jk([j.plan for j in active], [j.D for j in active], [j.J for j in active],
@@ -146,22 +225,26 @@ class Server:
                         j.result = {"J": j.J[0].clone(), "K": j.K[0].clone()}
                     done.append(j)
                 else:
-                    e, conv = j.scf.update(j.J[0], j.K[0], self.scf_conv)
+                    e, conv = j.scf.update(j.J[0].clone(), j.K[0].clone(), self.scf_conv)
                     j.iters += 1
                     if conv or j.iters >= self.scf_max_iter:
                         j.result = {"energy": e, "converged": conv, "iterations": j.iters}
                         done.append(j)
                     else:
-                        j.D = j.scf.D.unsqueeze(0).contiguous()
+                        j.D = j.scf.build_density().unsqueeze(0).contiguous()
             if done:
                 self.sync()
                 now = time.perf_counter() - t0
                 for j in done:
                     self._retire(j, now)
-                    used -= j.footprint
                     active.remove(j)
+                    retired.append(j)
+        free_retired()
         makespan = time.perf_counter() - t0
-        return summarize(jobs, makespan, {"ticks": self.ticks, "mean_batch": float(np.mean(self.batch_sizes))})
+        if self.pool is not None:
+            self.pool.shutdown(wait=True)
+        return summarize(jobs, makespan, {"ticks": self.ticks, "mean_batch": float(np.mean(self.batch_sizes)),
+                                          "prepared_ahead": self.prepared_ahead})
 
 
 def run_sequential(jobs: List[Job], scf_conv: float = 1e-8, scf_max_iter: int = 100, keep_results=False):
@@ -182,7 +265,7 @@ def run_sequential(jobs: List[Job], scf_conv: float = 1e-8, scf_max_iter: int = 
             if keep_results:
                 j.result = {"J": J[0].clone(), "K": K[0].clone()}
         else:
-            r = RHF(j.mol, plan=plan).kernel(conv_tol=scf_conv, max_iter=scf_max_iter)
+            r = RHF(j.mol, plan=plan, incremental=True).kernel(conv_tol=scf_conv, max_iter=scf_max_iter)
             j.result = {"energy": r.energy, "converged": r.converged, "iterations": r.iterations}
             j.iters = r.iterations
         plan.close()

@@ -36,6 +36,7 @@ def test_same_alone_and_in_the_mix(precision):
     jobs = make_jobs(reqs)
     stats = Server(precision=precision, max_slots=16).run(jobs, keep_results=True)
     assert stats["requests"] == len(reqs) and stats["mean_batch"] > 1.0
+    assert stats["prepared_ahead"] > 0             # plans were built ahead of admission
     tol = 1e-12 if precision == pkg.ERI_FP64 else 1e-9
     for j in jobs:
         plan = Plan(j.mol, precision=precision)
@@ -46,7 +47,7 @@ def test_same_alone_and_in_the_mix(precision):
             assert float((J[0] - j.result["J"]).abs().max()) <= tol * float(J.abs().max())
             assert float((K[0] - j.result["K"]).abs().max()) <= tol * float(K.abs().max())
         else:
-            r = RHF(j.mol, plan=plan).kernel(conv_tol=1e-8, max_iter=100)
+            r = RHF(j.mol, plan=plan, incremental=True).kernel(conv_tol=1e-8, max_iter=100)
             assert j.result["converged"] and r.converged
             assert abs(r.energy - j.result["energy"]) <= 1e-8
         plan.close()

@@ -69,6 +69,9 @@ class _FakeSCF:
         self.left -= 1
         return -1.0, self.left <= 0
 
+    def build_density(self):
+        return self.D
+
 
 def _server(**kw):
     from paper_2407_09700_gb300.serve import Server
@@ -84,7 +87,7 @@ def _server(**kw):
             job.finish = now
             job.plan = job.scf = None
 
-    return S(batch=_FakeBatch(kw.pop("delay", 0.002)), sync=lambda: None, **kw)
+    return S(batch=_FakeBatch(kw.pop("delay", 0.002)), sync=lambda: None, prefetch=0, **kw)
 
 
 def _jobs(spec):
@@ -116,6 +119,44 @@ def test_server_continuous_admission_and_latency():
     assert out["p50_latency_s"] == pytest.approx(float(np.percentile(lat, 50)))
     assert out["p99_latency_s"] == pytest.approx(float(np.percentile(lat, 99)))
     assert math.isfinite(out["throughput_req_s"]) and out["throughput_req_s"] > 0
+
+
+def test_server_prepares_ahead_and_frees_retired_plans_when_idle_or_needed():
+    """Arrived requests are prepared on the worker thread before their admission, within the
+    budget; retired plans are freed only when no job is active or an admission needs the
+    memory, and every prepared plan is freed by the end."""
+    from paper_2407_09700_gb300.serve import Server
+    log = []
+
+    class S(Server):
+        def _prepare(self, job):
+            log.append(("prepare", job.rid))
+            job.plan = object()
+
+        def _admit(self, job, now):
+            assert job.prepared is None or job.prepared.done() or job.prepared.result() is None
+            log.append(("admit", job.rid))
+            job.scf = _FakeSCF(job.mol) if job.kind == "scf" else None
+            job.D = job.J = job.K = torch.zeros((1, 1, 1))
+            job.admit = now
+
+        def _retire(self, job, now):
+            job.finish = now
+
+        def _destroy(self, job):
+            log.append(("free", job.rid))
+            job.plan = None
+
+    # budget 10, footprint 4: two jobs at a time; the third needs the first one's memory
+    jobs = _jobs([("scf", 3, 0.0, 4), ("jk", 0, 0.0, 4), ("jk", 0, 0.0, 4), ("jk", 0, 0.0, 4)])
+    srv = S(batch=_FakeBatch(0.002), sync=lambda: None, prefetch=4, hbm_budget=10, max_slots=4)
+    out = srv.run(jobs)
+    assert out["requests"] == 4 and srv.max_used <= 10
+    assert sorted(r for k, r in log if k == "prepare") == [0, 1, 2, 3][:len([1 for k, _ in log if k == "prepare"])]
+    assert sorted(r for k, r in log if k == "free") == [0, 1, 2, 3]
+    for rid in range(4):
+        assert log.index(("admit", rid)) < log.index(("free", rid))
+    assert all(j.plan is None for j in jobs)
 
 
 def test_server_rejects_a_request_larger_than_the_budget():
