@@ -4,9 +4,12 @@
 A step is one complete J/K build (screening, every class kernel, symmetrisation)
 of the medium workload: 30 atoms on a jittered 1.8 A lattice, 3s2p1d per atom
 with contraction depths 1..6, 450 Cartesian functions, one random PSD density
-(60 columns), tau = 1e-12, FP64 throughout.  It stands in for the paper's
-6-31G(d)-class Gly_n / RNA_n Fock builds (Sec. 5), whose inputs are not
-available.
+(60 columns), tau = 1e-12, FP64 throughout, through the library's default
+two-stream path.  It stands in for the paper's 6-31G(d)-class Gly_n / RNA_n Fock
+builds (Sec. 5), whose inputs are not available.  The same JSON line carries the
+other workloads (rank 0): the tiny build, the high-angular-momentum build (FP64 and
+mixed), the 120-atom RHF (20 iterations, FP64 and mixed), a reduced served workload,
+the mixed medium build, the J/K gradient and the CPU oracle's rate.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -51,6 +54,9 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision measurement")
     ap.add_argument("--no-grad", action="store_true", help="skip the gradient measurement")
     ap.add_argument("--no-serve", action="store_true", help="skip the served-workload measurement")
+    ap.add_argument("--no-scf", action="store_true", help="skip the 120-atom RHF measurement")
+    ap.add_argument("--no-extra", action="store_true", help="skip the tiny and high-l builds")
+    ap.add_argument("--scf-natm", type=int, default=120, help="atoms of the RHF workload (120 = its recipe)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target wall time of the oracle sample")
     return ap.parse_args()
 
@@ -232,17 +238,231 @@ def run_reference(args):
     return 0
 
 
+# ---------------------------------------------------------------- per-kernel work counts
+
+GOLDEN = os.path.join(ROOT, "tests", "golden", "oracle_class_ops.json")
+
+
+def load_oracle_ops():
+    """Per-class operation counts of the OS/HGP oracle (written by
+    tests/golden/make_oracle_class_ops.py from the oracle's instrumented counter)."""
+    with open(GOLDEN) as f:
+        return json.load(f)["classes"]
+
+
+def ncart(l):
+    return (l + 1) * (l + 2) // 2
+
+
+def oracle_ops(table, r, nD=1):
+    """Oracle operations for the primitive and contracted quartets one launch evaluated."""
+    c = table[f"{r['la']}{r['lb']}{r['lc']}{r['ld']}"]
+    return (c["per_prim"] * r["prim_quartets"]
+            + (c["hrr"] + nD * c["digest_per_density"]) * r["quartets"])
+
+
+def rys_model_flops(r, nD=1):
+    """The Rys-model count of the scope table per launch: per primitive quartet N roots at
+    28 FLOP (two degree-7 polynomials), 3 axes x N roots x 3 FLOP per 2D-table entry and Eq. 1
+    at 3 FLOP per Cartesian term and root; per contracted quartet 12 FLOP per value and density
+    (the six digestion FMAs)."""
+    la, lb, lc, ld = r["la"], r["lb"], r["lc"], r["ld"]
+    N = (la + lb + lc + ld) // 2 + 1
+    nI = (la + lb + 1) * (lc + ld + 1)
+    nabcd = ncart(la) * ncart(lb) * ncart(lc) * ncart(ld)
+    return (r["prim_quartets"] * (28 * N + 3 * N * 3 * nI + 3 * N * nabcd)
+            + r["quartets"] * 12 * nabcd * nD)
+
+
+def kernel_name(r):
+    prec = "float" if r["fp32"] else "double"
+    if r["specialised"]:
+        return f"eri_small_kernel<{r['la']}, {r['lb']}, {r['lc']}, {r['ld']}, {prec}>"
+    xy = "true" if r["shared_products"] else "false"
+    return f"eri_class_kernel<{r['team_size']}, {prec}, {xy}>"
+
+
+def profile_build(plan, D, table, nD=1):
+    """One build with per-launch CUDA events (one stream, each launch timed alone): per kernel
+    instantiation its time, launches and work by the three counts."""
+    plan.set_profiling(True)
+    plan.jk(D)
+    recs = plan.launch_records()
+    plan.set_profiling(False)
+    per = {}
+    for r in recs:
+        e = per.setdefault(kernel_name(r), {"ms": 0.0, "launches": 0, "model_flops": 0.0, "model_flops_fp32": 0.0,
+                                            "oracle_ops": 0.0, "rys_model_flops": 0.0, "fp32": r["fp32"]})
+        e["ms"] += r["ms"]
+        e["launches"] += 1
+        e["model_flops"] += r["model_flops"]
+        e["model_flops_fp32"] += r["model_flops_fp32"]
+        e["oracle_ops"] += oracle_ops(table, r, nD)
+        e["rys_model_flops"] += rys_model_flops(r, nD)
+    return per, recs
+
+
+def roofline_of(per, peak64, peak32=None):
+    """Roofline of the dominant kernel (most time in the profiled build) in oracle operations
+    (the reported fraction), with the kernel's own operation model and the Rys model beside it."""
+    name, d = max(per.items(), key=lambda kv: kv[1]["ms"])
+    t = d["ms"] / 1e3
+    peak = peak32 if (d["fp32"] and peak32) else peak64
+    total = sum(v["ms"] for v in per.values())
+    ach = d["oracle_ops"] / t / 1e12
+    return {"bound": "alu", "kernel": name, "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+            "traffic": None,
+            "model_achieved": d["model_flops"] / t / 1e12, "model_frac": d["model_flops"] / t / 1e12 / peak,
+            "rys_model_achieved": d["rys_model_flops"] / t / 1e12,
+            "rys_model_frac": d["rys_model_flops"] / t / 1e12 / peak,
+            "share_of_kernel_time": d["ms"] / total, "launches": d["launches"],
+            "peak_kind": ("measured FP32 FMA loop on this GPU" if (d["fp32"] and peak32) else
+                          "measured FP64 FMA loop on this GPU (nominal 152 SM x 4 flop/clk x 2.07 GHz = "
+                          "1.26 TFLOP/s); MEASURED_PEAKS.json has HBM and bf16 only"),
+            "flops_kind": "achieved / frac: operations of the OS/HGP oracle (its instrumented counter per class, "
+                          "tests/golden/oracle_class_ops.json) for the primitive and contracted quartets the "
+                          "launches evaluated; model_*: the kernel's own operation count (FMA = 2); rys_model_*: "
+                          "the Rys-model count (roots, 2D tables, Eq. 1 at 3 FLOP per term, digestion)",
+            "traffic_note": "null: pair data, D, J and K stay in L2 (DRAM bytes per launch do not grow with its "
+                            "work; see profiles/)"}
+
+
+def shares_of(per):
+    total = sum(v["ms"] for v in per.values())
+    return {k: round(v["ms"] / total, 4) for k, v in sorted(per.items(), key=lambda kv: -kv[1]["ms"])[:8]}
+
+
+def time_builds(plan, D, J, K, steps, flush, stream):
+    """Per-build CUDA-event times (seconds) on the default two-stream path, L2 flushed before
+    each build outside the events."""
+    import torch
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        flush.zero_()
+        evs[k][0].record(stream)
+        plan.jk(D, J, K)
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) / 1e3 for a, b in evs]
+
+
+def launches_per_build(st):
+    # the density-maxima kernel, the class kernels, three compaction kernels (counts, scan,
+    # ordered writes) per FP64 class launch, two symmetrisations
+    n = st["nclasses_launched"]
+    return 1 + n + 3 * n + 2
+
+
+# ---------------------------------------------------------------- legs of the JSON line (rank 0)
+
+def leg_mixed(pkg, mol, D, J64, K64, steps, flush, stream, table, peak64, peak32):
+    import torch
+    plan_m = pkg.Plan(mol, precision=pkg.ERI_MIXED, mixed_thresh=MIXED_THRESH)
+    Jm = torch.empty_like(D)
+    Km = torch.empty_like(D)
+    plan_m.jk(D, Jm, Km)
+    ts = time_builds(plan_m, D, Jm, Km, steps, flush, stream)
+    stm = plan_m.stats()
+    per, _ = profile_build(plan_m, D, table)
+    t = statistics.median(ts)
+    f64 = sum(v["model_flops"] - v["model_flops_fp32"] for v in per.values())
+    f32 = sum(v["model_flops_fp32"] for v in per.values())
+    pt = sum(v["ms"] for v in per.values()) / 1e3
+    out = {"value": 1.0 / t, "unit": "J/K builds/s", "ms_per_step": 1e3 * t, "steps": steps,
+           "quartets_per_s": stm["quartets_computed"] / t,
+           "fp32_quartet_fraction": stm["quartets_fp32"] / max(1, stm["quartets_computed"]),
+           "mixed_thresh": MIXED_THRESH,
+           "split": "FP32 recurrences where the transfer-aware bound Qe_ij Qe_kl max|D| <= mixed_thresh",
+           "max_abs_dJ_vs_fp64": float((Jm - J64).abs().max()), "max_abs_dK_vs_fp64": float((Km - K64).abs().max()),
+           "fp64_pipe_frac": f64 / pt / 1e12 / peak64, "fp32_pipe_frac": f32 / pt / 1e12 / peak32,
+           "kernel_shares": shares_of(per)}
+    plan_m.close()
+    return out
+
+
+def leg_small_build(pkg, mol, name, steps, flush, stream, table, peak64, peak32, J64=None, K64=None):
+    """FP64 and mixed builds of one workload: builds/s, quartets/s, dominant-kernel roofline."""
+    import torch
+    D = torch.from_numpy(mol.D).cuda()
+    out = {"workload": name}
+    ref = None
+    for tag, prec in (("fp64", pkg.ERI_FP64), ("mixed", pkg.ERI_MIXED)):
+        plan = pkg.Plan(mol, precision=prec, mixed_thresh=MIXED_THRESH)
+        J = torch.empty_like(D)
+        K = torch.empty_like(D)
+        plan.jk(D, J, K)
+        ts = time_builds(plan, D, J, K, steps, flush, stream)
+        st = plan.stats()
+        per, _ = profile_build(plan, D, table)
+        t = statistics.median(ts)
+        leg = {"value": 1.0 / t, "unit": "J/K builds/s", "ms_per_step": 1e3 * t, "steps": steps,
+               "quartets_per_build": st["quartets_computed"], "quartets_per_s": st["quartets_computed"] / t,
+               "roofline": roofline_of(per, peak64, peak32), "kernel_shares": shares_of(per)}
+        if tag == "fp64":
+            ref = (J.clone(), K.clone())
+        else:
+            leg["fp32_quartet_fraction"] = st["quartets_fp32"] / max(1, st["quartets_computed"])
+            leg["max_abs_dJ_vs_fp64"] = float((J - ref[0]).abs().max())
+            leg["max_abs_dK_vs_fp64"] = float((K - ref[1]).abs().max())
+            leg["speedup_vs_fp64"] = out["fp64"]["ms_per_step"] / leg["ms_per_step"]
+        out[tag] = leg
+        plan.close()
+    return out
+
+
+def leg_scf(pkg, natm, iters):
+    """The 120-atom RHF recipe, 20 iterations, FP64 and mixed (PySCF-style incremental
+    builds after the first); energies, J/K times, and J/K of the FP64 run's final density
+    through both plans (full builds) compared."""
+    import numpy as np
+    import torch
+    from paper_2407_09700_gb300.scf import RHF
+    from workloads import config_scf
+    mol = config_scf(seed=0, natm=natm)
+    out = {"workload": f"RHF, {natm}-atom jittered 1.8 A lattice, 30% 3s2p1d (Z=6) / 70% 2s1p (Z=1), "
+                       f"6-31G(d)-like depths, {mol.nbf} Cartesian functions, core guess, DIIS (8), "
+                       f"{iters} iterations, incremental J/K builds after the first",
+           "iterations": iters, "nbf": mol.nbf}
+    plans = {}
+    for tag, prec in (("fp64", pkg.ERI_FP64), ("mixed", pkg.ERI_MIXED)):
+        t0 = time.perf_counter()
+        scf = RHF(mol, precision=prec, mixed_thresh=MIXED_THRESH, incremental=True)
+        setup = time.perf_counter() - t0
+        r = scf.kernel(fixed_iters=iters)
+        out[tag] = {"energy": r.energy, "setup_s": setup, "scf_s": r.total_seconds,
+                    "jk_s_total": float(sum(r.jk_seconds)), "jk_s_first_full_build": float(r.jk_seconds[0]),
+                    "jk_s_mean_incremental": float(np.mean(r.jk_seconds[1:])) if len(r.jk_seconds) > 1 else None,
+                    "full_builds_per_s": 1.0 / float(r.jk_seconds[0]),
+                    "energy_change_last_iter": abs(r.energies[-1] - r.energies[-2]) if len(r.energies) > 1 else None}
+        plans[tag] = (scf.plan, r.D)
+    out["abs_dE_mixed_vs_fp64"] = abs(out["fp64"]["energy"] - out["mixed"]["energy"])
+    Dfin = plans["fp64"][1].unsqueeze(0).contiguous()
+    J64, K64 = plans["fp64"][0].jk(Dfin)
+    Jm, Km = plans["mixed"][0].jk(Dfin)
+    torch.cuda.synchronize()
+    out["max_abs_dJ_mixed_vs_fp64"] = float((Jm - J64).abs().max())
+    out["max_abs_dK_mixed_vs_fp64"] = float((Km - K64).abs().max())
+    out["fp32_quartet_fraction_full_build"] = plans["mixed"][0].stats()["quartets_fp32"] / max(
+        1, plans["mixed"][0].stats()["quartets_computed"])
+    for p, _ in plans.values():
+        p.close()
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
 
     import paper_2407_09700_gb300 as pkg
-    from workloads import config_medium
+    from workloads import config_high_l, config_medium, config_tiny
 
+    t_start = time.perf_counter()
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
     dist = Dist("nccl")
     pkg.build()
+    table = load_oracle_ops()
     mol = config_medium(seed=args.seed, natm=args.natm)
     nbf = mol.nbf
     plan = pkg.Plan(mol)
@@ -257,50 +477,26 @@ def run_ours(args):
         plan.jk(D, J, K)
     torch.cuda.synchronize()
 
-    # ---- device-timed region: inputs resident, L2 flushed between steps
-    plan.set_profiling(True)
+    # ---- device-timed region: the default two-stream path, inputs resident, L2 flushed
+    #      before every build (outside the events)
     clk = Clocks(gpu_index(local))
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    per_kernel = {}
     dist.barrier()
     torch.cuda.synchronize()
     clk.start()
     time.sleep(0.3)
-    for k in range(args.steps):
-        flush.zero_()
-        ev[k][0].record(stream)
-        plan.jk(D, J, K)
-        ev[k][1].record(stream)
-        recs = plan.launch_records()            # syncs this step's stream; outside the events
-        for r in recs:
-            prec = "float" if r["fp32"] else "double"
-            if r["specialised"]:
-                key = f"eri_small_kernel<{r['la']}, {r['lb']}, {r['lc']}, {r['ld']}, {prec}>"
-            else:
-                xy = "true" if r["shared_products"] else "false"
-                key = f"eri_class_kernel<{r['team_size']}, {prec}, {xy}>"
-            e = per_kernel.setdefault(key, {"ms": 0.0, "flops": 0.0, "launches": 0})
-            e["ms"] += r["ms"]
-            e["flops"] += r["model_flops"]
-            e["launches"] += 1
-    torch.cuda.synchronize()
+    ts = time_builds(plan, D, J, K, args.steps, flush, stream)
     dist.barrier()
     clocks = clk.stop()
-    plan.set_profiling(False)
-    t_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    t_s = sum(ts)
     t_max = dist.max(t_s)
     st = plan.stats()
     nsteps_total = args.steps * ws
     value = replica_throughput(args.steps, ws, t_max)
     quartets_per_s = st["quartets_computed"] * nsteps_total / t_max
-    # per build: the density-maxima kernel, the class kernels, three compaction kernels
-    # (counts, scan, ordered writes) per FP64 class launch, and the two symmetrisations
-    launches_per_step = 1 + st["nclasses_launched"] + 3 * st["nclasses_launched"] + 2
 
-    # dominant kernel: the class-kernel instantiation with the most time in the region
-    dom_name, dom = max(per_kernel.items(), key=lambda kv: kv[1]["ms"])
-    achieved = dom["flops"] / (dom["ms"] / 1e3) / 1e12
-    all_ms = sum(v["ms"] for v in per_kernel.values())
+    # ---- kernel shares and the dominant kernel's roofline from one separately profiled build
+    per, _ = profile_build(plan, D, table)
+    roof = roofline_of(per, fp64_peak)
 
     # ---- end to end: host buffers through the C-ABI (copies inside the timed call)
     Dh = torch.from_numpy(mol.D).pin_memory()
@@ -317,47 +513,42 @@ def run_ours(args):
         if rc != 0:
             raise RuntimeError(lib.eri_last_error().decode())
     host_call()
+    n_e2e = max(3, args.steps // 4)
     dist.barrier()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(n_e2e):
         host_call()
     te = dist.max(time.perf_counter() - t0)
-    e2e = nsteps_total / te
+    e2e = n_e2e * ws / te
     bytes_mat = 8 * nbf * nbf
-
     # parity spot check of the timed result against the e2e result (same algorithm, host copies)
     assert float((J.cpu() - Jh).abs().max()) < 1e-9
 
-    # ---- mixed precision on the same workload (FP32 recurrences where the bound <= MIXED_THRESH)
+    wall = {"medium_fp64_and_e2e": time.perf_counter() - t_start}
+    n_side = max(3, args.steps // 4)
     mixed = None
+    t1 = time.perf_counter()
     if not args.no_mixed:
-        plan_m = pkg.Plan(mol, precision=pkg.ERI_MIXED, mixed_thresh=MIXED_THRESH)
-        Jm = torch.empty_like(D)
-        Km = torch.empty_like(D)
-        for _ in range(max(1, args.warmup - 2)):
-            plan_m.jk(D, Jm, Km)
-        torch.cuda.synchronize()
-        evm = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-        dist.barrier()
-        for k in range(args.steps):
-            flush.zero_()
-            evm[k][0].record(stream)
-            plan_m.jk(D, Jm, Km)
-            evm[k][1].record(stream)
-        torch.cuda.synchronize()
-        tm = dist.max(sum(a_.elapsed_time(b_) for a_, b_ in evm) / 1e3)
-        stm = plan_m.stats()
-        mixed = {"value": nsteps_total / tm, "unit": "J/K builds/s", "ms_per_step": 1e3 * tm / args.steps,
-                 "quartets_per_s": stm["quartets_computed"] * nsteps_total / tm,
-                 "fp32_quartet_fraction": stm["quartets_fp32"] / max(1, stm["quartets_computed"]),
-                 "mixed_thresh": MIXED_THRESH,
-                 "max_abs_dJ_vs_fp64": float((Jm - J).abs().max()),
-                 "max_abs_dK_vs_fp64": float((Km - K).abs().max()),
-                 "speedup_vs_fp64": (nsteps_total / tm) / value}
-        plan_m.close()
+        mixed = leg_mixed(pkg, mol, D, J, K, n_side, flush, stream, table, fp64_peak, fp32_peak)
 
+    wall["mixed"] = time.perf_counter() - t1
+    extra = {}
+    t1 = time.perf_counter()
+    if rank == 0 and not args.no_extra:
+        tiny = config_tiny(seed=args.seed)
+        extra["tiny"] = leg_small_build(pkg, tiny, "tiny J/K build: 3 atoms in a 3 A box, 2s1p per atom, K = 3, "
+                                        f"beta = 3, {tiny.nbf} Cartesian functions, PSD density (5 columns), "
+                                        "tau 1e-12", 50, flush, stream, table, fp64_peak, fp32_peak)
+        hl = config_high_l(seed=args.seed)
+        extra["high_l"] = leg_small_build(pkg, hl, "high-l J/K build: 12 atoms, jittered 1.8 A lattice, s p d f g "
+                                          f"per atom, depths 1-3, beta 2.2, {hl.nbf} Cartesian functions, PSD "
+                                          "density (40 columns), tau 1e-12", n_side, flush, stream, table,
+                                          fp64_peak, fp32_peak)
+
+    wall["tiny_high_l"] = time.perf_counter() - t1
     # ---- J/K energy gradient (FP64) on the 12-atom cut of the same recipe, beside its J/K build
     grad = None
+    t1 = time.perf_counter()
     if not args.no_grad:
         mg = config_medium(seed=args.seed, natm=12)
         plan_g = pkg.Plan(mg)
@@ -367,7 +558,7 @@ def run_ours(args):
         plan_g.jk_grad(Dg, gJ, gK)
         plan_g.jk(Dg)
         torch.cuda.synchronize()
-        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0, e1, e2, e3 = (torch.cuda.Event(enable_timing=True) for _ in range(4))
         flush.zero_()
         e0.record(stream)
         plan_g.jk_grad(Dg, gJ, gK)
@@ -375,7 +566,6 @@ def run_ours(args):
         flush.zero_()
         e2.record(stream)
         plan_g.jk(Dg)
-        e3 = torch.cuda.Event(enable_timing=True)
         e3.record(stream)
         torch.cuda.synchronize()
         gst = plan_g.grad_stats()
@@ -386,28 +576,43 @@ def run_ours(args):
                 "max_abs_sum_over_atoms": float(max(gJ.sum(0).abs().max(), gK.sum(0).abs().max()))}
         plan_g.close()
 
-    # ---- served workload (rank 0): continuous batching (mixed) against one-at-a-time FP64
+    wall["grad"] = time.perf_counter() - t1
+    scf = None
+    t1 = time.perf_counter()
+    if rank == 0 and not args.no_scf:
+        scf = leg_scf(pkg, args.scf_natm, 20)
+    wall["scf"] = time.perf_counter() - t1
+    t1 = time.perf_counter()
+
+    # ---- served workload (rank 0), reduced: continuous batching (mixed and FP64) against
+    #      one-at-a-time FP64
     served = None
     if rank == 0 and not args.no_serve:
         from workloads import config_served_requests
         from paper_2407_09700_gb300.serve import Server, make_jobs, run_sequential
         reqs = config_served_requests(seed=args.seed, nreq=32, mean_interarrival_s=0.02, natm_range=(5, 15))
         Server().run(make_jobs(reqs[:1], natm_cap=5))        # warm kernels and allocator
+        keys = ("throughput_req_s", "p50_latency_s", "p99_latency_s", "makespan_s", "mean_batch")
         sv = Server(hbm_budget=64 << 30, max_slots=32).run(make_jobs(reqs))
+        sv64 = Server(precision=pkg.ERI_FP64, hbm_budget=64 << 30, max_slots=32).run(make_jobs(reqs))
         sq = run_sequential(make_jobs(reqs))
-        served = {"workload": "32 requests, exponential inter-arrival mean 20 ms (50 req/s), atoms log-uniform "
-                              "[5, 15], 30% RHF to 1e-8 Ha, 70% single J/K; heavy/light 3s2p1d/2s1p recipe",
-                  "served_mixed": {k: sv[k] for k in ("throughput_req_s", "p50_latency_s", "p99_latency_s",
-                                                      "makespan_s", "mean_batch")},
-                  "sequential_fp64": {k: sq[k] for k in ("throughput_req_s", "p50_latency_s", "p99_latency_s",
-                                                         "makespan_s")}}
+        served = {"workload": "REDUCED served workload (the recipe's 512 requests of 5-80 atoms run in a dedicated "
+                              "call, profiles/served_full.md): 32 requests, exponential inter-arrival mean 20 ms "
+                              "(50 req/s), atoms log-uniform [5, 15], 30% RHF to 1e-8 Ha, 70% single J/K; "
+                              "heavy/light 3s2p1d/2s1p recipe",
+                  "batched_mixed": {k: sv[k] for k in keys if k in sv},
+                  "batched_fp64": {k: sv64[k] for k in keys if k in sv64},
+                  "sequential_fp64": {k: sq[k] for k in keys if k in sq}}
 
+    wall["served"] = time.perf_counter() - t1
     cpu = None
+    t1 = time.perf_counter()
     if rank == 0 and not args.no_cpu_baseline:
         b, qs, cores, desc = oracle_sample_rate(mol, args.cpu_seconds)
         cpu = {"value": b, "unit": "J/K builds/s", "cores": cores, "kind": "oracle", "sample": desc,
                "quartets_per_s": qs}
 
+    wall["cpu_baseline"] = time.perf_counter() - t1
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "J/K builds/s", "n_gpus": ws, "steps": args.steps,
@@ -415,28 +620,27 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload_name(args.natm), "seed": args.seed, "nbf": nbf, "natm": mol.natm,
                        "nshell": mol.nshell, "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                       "path": "eri_jk default (class launches alternating between two streams)",
                        "l2": "flushed (256 MB write) before every timed step; events exclude the flush"},
             "quartets_per_s": quartets_per_s,
             "quartets_per_build": st["quartets_computed"],
             "prim_quartets_per_build": st["prim_quartets"],
             "model_tflops": st["model_flops"] / (t_max / nsteps_total) / 1e12,
-            "roofline": {"bound": "alu", "kernel": dom_name, "achieved": achieved, "peak": fp64_peak,
-                         "unit": "TFLOP/s", "frac": achieved / fp64_peak, "traffic": None,
-                         "peak_kind": "measured FP64 FMA loop on this GPU (nominal 152 SM x 4 flop/clk x "
-                                      "2.07 GHz = 1.26 TFLOP/s)",
-                         "share_of_kernel_time": dom["ms"] / all_ms,
-                         "flops_kind": "FP64 operations of the class kernel's algorithm per class "
-                                       "(FMA = 2), times primitive quartets / quartets counted on device"},
+            "roofline": roof,
             "fp32_fma_peak_tflops": fp32_peak,
             "e2e": {"value": e2e, "unit": "J/K builds/s", "h2d_bytes_per_step": bytes_mat,
-                    "d2h_bytes_per_step": 2 * bytes_mat},
-            "gpu_launches": launches_per_step * args.steps,
+                    "d2h_bytes_per_step": 2 * bytes_mat, "steps": n_e2e},
+            "gpu_launches": launches_per_build(st) * args.steps,
             "clocks": clocks,
             "cpu_baseline": cpu,
             "mixed": mixed,
+            "tiny": extra.get("tiny"),
+            "high_l": extra.get("high_l"),
+            "scf": scf,
             "grad": grad,
             "served": served,
-            "kernel_shares": {k: round(v["ms"] / all_ms, 4) for k, v in sorted(per_kernel.items(), key=lambda kv: -kv[1]["ms"])[:8]},
+            "kernel_shares": shares_of(per),
+            "leg_wall_s": {k: round(v, 1) for k, v in wall.items()},
         }
         print(json.dumps(line), flush=True)
     dist.close()
