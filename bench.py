@@ -279,6 +279,8 @@ def kernel_name(r):
     if r["specialised"]:
         return f"eri_small_kernel<{r['la']}, {r['lb']}, {r['lc']}, {r['ld']}, {prec}>"
     xy = "true" if r["shared_products"] else "false"
+    if r.get("compiled_class"):
+        return f"eri_class_kernel<{r['team_size']}, {prec}, {xy}, {r['la']}{r['lb']}{r['lc']}{r['ld']}>"
     return f"eri_class_kernel<{r['team_size']}, {prec}, {xy}>"
 
 

@@ -242,6 +242,8 @@ typedef struct {
   int shared_products;            /* 1 when the launch formed each I_x I_y product once per team in
                                      shared memory; 0 for lane programs (products reused within a
                                      lane) */
+  int compiled_class;             /* 1 when the team kernel was compiled for this one class (its root
+                                     count and recurrence sizes constants) */
 } eri_launch_record;
 
 /* Turn per-launch CUDA-event timing of later eri_jk calls on (1) or off (0). */

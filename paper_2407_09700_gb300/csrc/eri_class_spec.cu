@@ -12,6 +12,17 @@
 
 extern "C" int erik_upload_cart_tables_spec(void) { return (int)upload_cart_table(); }
 
+// 1 when a kernel compiled for class (la lb | lc ld) exists for this team size (FP64).
+extern "C" int erik_class_spec_available(int ts, int la, int lb, int lc, int ld) {
+  if (ts != 8) return 0;
+  const int cls = 1000 * la + 100 * lb + 10 * lc + ld;
+#define SPEC_HAS(C) \
+  if (cls == C) return 1;
+  SPEC_CLASSES(SPEC_HAS)
+#undef SPEC_HAS
+  return 0;
+}
+
 extern "C" int erik_launch_class_spec(int ts, int xy, const KernelArgs* a, int grid, int smem_bytes, void* stream,
                                       int* rc) {
   if (ts != 8) return 0;

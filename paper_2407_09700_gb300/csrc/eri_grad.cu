@@ -172,153 +172,187 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : 2)) eri_grad_kernel(const 
     }
     const int boff = active ? bra->prim_off : 0, koff = active ? ket->prim_off : 0;
 
-    // ---- 1. the four contracted sets, in passes of TS * GSLOTS values
-    for (int pass = 0; pass < g.npass; ++pass) {
-      const int o0 = pass * TS * GSLOTS;
-      uint32_t pkd[GSLOTS];
-      double acc[GSLOTS];
+    // ---- 1. the four contracted sets, in passes of TS * GSLOTS values.  With several passes
+    //      the batches of primitive quartets run outside the passes: the roots and 2D tables
+    //      of a batch are evaluated once and each pass carries its partial sums in the team's
+    //      scratch from batch to batch (as in the J/K class kernel).
+    int o0 = 0, kcnt = 0;
+    uint32_t pkd[GSLOTS];
+    double acc[GSLOTS];
+    uint32_t gm = 0u;
+    auto slot_valid = [&](int k) -> bool {
+      const int o = o0 + k * TS + tl;
+      if (!(k < kcnt && o < g.nslot)) return false;
+      const uint32_t p = (TS == 1) ? __ldg(g.outidx + o0 + k) : pkd[k];
+      return !(p >> 31);
+    };
+    auto begin_pass = [&](int pass, bool from_scr) {
+      o0 = pass * TS * GSLOTS;
+      kcnt = min(GSLOTS, (g.nslot - o0 + TS - 1) / TS);
 #pragma unroll
       for (int k = 0; k < GSLOTS; ++k) {
         const int o = o0 + k * TS + tl;
         if (TS > 1) pkd[k] = (o < g.nslot) ? __ldg(g.outidx + o) : (1u << 31);
         acc[k] = 0.0;
       }
-      const int kcnt = min(GSLOTS, (g.nslot - o0 + TS - 1) / TS);
-      const uint32_t gm = __ldg(g.gmask + pass);
-
-      for (int q0 = 0; q0 < maxq; q0 += bp) {
-        const int nbt = min(bp, nq - q0);
-        // a. primitive-quartet scalars
-        for (int j = tl; j < bp; j += TS) {
-          if (j < nbt) {
-            const int q = q0 + j;
-            const PrimPair* x = a.prims + boff + q / npk;
-            const PrimPair* y = a.prims + koff + q % npk;
-            const double zeta = x->zeta, eta = y->zeta;
-            const double rd = rsqrt(zeta + eta);
-            const double PQ0 = x->P[0] - y->P[0], PQ1 = x->P[1] - y->P[1], PQ2 = x->P[2] - y->P[2];
-            const double inv_s = rd * rd;
-            const double T = zeta * eta * inv_s * fma(PQ0, PQ0, fma(PQ1, PQ1, PQ2 * PQ2));
-            int ti;
-            double xx, invT, rsqT;
-            rys_locate(T, a.rys_tcut_d, ti, xx, invT, rsqT);
-            const int od = j * NPD;
-            sd[od + 0] = xx;
-            sd[od + 1] = invT;
-            sd[od + 2] = rsqT;
-            sd[od + 3] = __longlong_as_double((long long)ti);
-            const double rz = eta * inv_s, re = zeta * inv_s;
-            const int o = j * GNPR;
-            sr[o + 0] = x->PA[0]; sr[o + 1] = x->PA[1]; sr[o + 2] = x->PA[2];
-            sr[o + 3] = y->PA[0]; sr[o + 4] = y->PA[1]; sr[o + 5] = y->PA[2];
-            sr[o + 6] = rz * PQ0; sr[o + 7] = rz * PQ1; sr[o + 8] = rz * PQ2;
-            sr[o + 9] = re * PQ0; sr[o + 10] = re * PQ1; sr[o + 11] = re * PQ2;
-            sr[o + 12] = 0.5 * inv_s;
-            sr[o + 13] = x->hz * rz;
-            sr[o + 14] = y->hz * re;
-            sr[o + 15] = x->E * y->E * rd;
-            sr[o + 16] = x->hz;
-            sr[o + 17] = y->hz;
-            sr[o + 18] = 2.0 * x->alpha;
-            sr[o + 19] = 2.0 * (zeta - x->alpha);
-            sr[o + 20] = 2.0 * y->alpha;
-          }
-        }
-        __syncwarp();
-        // b. roots, weights and the 2D tables per (primitive, root), or per (primitive, root,
-        //    axis) when that fills more of the team's lanes
-        if (TS > 1 && g.split3) {
-          for (int tk = tl; tk < bp * N * 3; tk += TS) {
-            const int jn = tk / 3, ax = tk - jn * 3;
-            const int j = jn / N, n = jn - (jn / N) * N;
-            if (j < nbt) {
-              const int od = j * NPD, o = j * GNPR;
-              double u, w;
-              rys_root(a.rys_coef, a.rys_au, a.rys_aw, N, (int)__double_as_longlong(sd[od + 3]), sd[od + 0],
-                       sd[od + 1], sd[od + 2], n, u, w);
-              const double B00 = u * sr[o + 12];
-              const double B10 = fma(-u, sr[o + 13], sr[o + 16]);
-              const double B01 = fma(-u, sr[o + 14], sr[o + 17]);
-              const double Cax = fma(-u, sr[o + 6 + ax], sr[o + 0 + ax]);
-              const double Cpx = fma(u, sr[o + 9 + ax], sr[o + 3 + ax]);
-              const double I00 = (ax == 2) ? w * sr[o + 15] : 1.0;
-              const int gt = S_2D + ((j * 6 + ax) * N + n) * nI;
-              rys_2d1<double>(sr, gt, Le2, Lf2, I00, Cax, Cpx, B00, B10, B01);
-              if (ax == 2) {
-                const double w1 = sr[o + 18], w2 = sr[o + 19], w3 = sr[o + 20];
-                for (int i = 0; i < nI; ++i) {
-                  const double z = sr[gt + i];
-                  sr[gt + N * nI + i] = w1 * z;
-                  sr[gt + 2 * N * nI + i] = w2 * z;
-                  sr[gt + 3 * N * nI + i] = w3 * z;
-                }
-              }
-            }
-          }
-        } else {
-          for (int tk = tl; tk < bp * N; tk += TS) {
-            const int j = tk / N, n = tk - (tk / N) * N;
-            if (j < nbt) {
-              const int od = j * NPD, o = j * GNPR;
-              double u, w;
-              rys_root(a.rys_coef, a.rys_au, a.rys_aw, N, (int)__double_as_longlong(sd[od + 3]), sd[od + 0],
-                       sd[od + 1], sd[od + 2], n, u, w);
-              const double B00 = u * sr[o + 12];
-              const double B10 = fma(-u, sr[o + 13], sr[o + 16]);
-              const double B01 = fma(-u, sr[o + 14], sr[o + 17]);
-              const double wt = w * sr[o + 15];
-              const double C[3] = {fma(-u, sr[o + 6], sr[o + 0]), fma(-u, sr[o + 7], sr[o + 1]),
-                                   fma(-u, sr[o + 8], sr[o + 2])};
-              const double Cp[3] = {fma(u, sr[o + 9], sr[o + 3]), fma(u, sr[o + 10], sr[o + 4]),
-                                    fma(u, sr[o + 11], sr[o + 5])};
-              const int g0 = S_2D + ((j * 6 + 0) * N + n) * nI;
-              const int og[3] = {g0, g0 + N * nI, g0 + 2 * N * nI};
-              rys_2d3<double>(sr, og, Le2, Lf2, wt, C, Cp, B00, B10, B01);
-              // the I_z table scaled by the primitive weights 2 alpha, 2 beta, 2 gamma
-              const double w1 = sr[o + 18], w2 = sr[o + 19], w3 = sr[o + 20];
-              for (int i = 0; i < nI; ++i) {
-                const double z = sr[og[2] + i];
-                sr[og[2] + N * nI + i] = w1 * z;
-                sr[og[2] + 2 * N * nI + i] = w2 * z;
-                sr[og[2] + 3 * N * nI + i] = w3 * z;
-              }
-            }
-          }
-        }
-        __syncwarp();
-        // c. assembly and contraction in registers by lane programs: a slot that starts a
-        //    group forms the group's I_x I_y product, each value adds product x weighted I_z
-        for (int j = 0; j < bp; ++j) {
-          if (j < nbt) {
-            for (int n = 0; n < N; ++n) {
-              const int gx = S_2D + ((j * 6 + 0) * N + n) * nI;
-              const int gy = gx + N * nI;
-              const int gz = gy + N * nI;
-              double v = 0.0;
+      if (from_scr && active) {
 #pragma unroll
-              for (int k = 0; k < GSLOTS; ++k) {
-                if (k < kcnt) {
-                  const uint32_t p = (TS == 1) ? __ldg(g.outidx + o0 + k) : pkd[k];
-                  if ((gm >> k) & 1u) v = sr[gx + (int)(p & 0xffu)] * sr[gy + (int)((p >> 8) & 0xffu)];
-                  acc[k] = fma(v, sr[gz + (int)((p >> 16) & 0xfffu)], acc[k]);
-                }
-              }
-            }
-          }
-        }
-        __syncwarp();
+        for (int k = 0; k < GSLOTS; ++k)
+          if (slot_valid(k)) acc[k] = scr[__ldg(g.dst + o0 + k * TS + tl)];
       }
+      gm = __ldg(g.gmask + pass);
+    };
+    auto end_pass = [&]() {
       if (active) {
 #pragma unroll
-        for (int k = 0; k < GSLOTS; ++k) {
-          const int o = o0 + k * TS + tl;
-          if (k < kcnt && o < g.nslot) {
-            const uint32_t p = (TS == 1) ? __ldg(g.outidx + o0 + k) : pkd[k];
-            if (!(p >> 31)) scr[__ldg(g.dst + o)] = acc[k];
+        for (int k = 0; k < GSLOTS; ++k)
+          if (slot_valid(k)) scr[__ldg(g.dst + o0 + k * TS + tl)] = acc[k];
+      }
+    };
+    auto batch_tables = [&](int q0, int nbt) {
+      // a. primitive-quartet scalars
+      for (int j = tl; j < bp; j += TS) {
+        if (j < nbt) {
+          const int q = q0 + j;
+          const PrimPair* x = a.prims + boff + q / npk;
+          const PrimPair* y = a.prims + koff + q % npk;
+          const double zeta = x->zeta, eta = y->zeta;
+          const double rd = rsqrt(zeta + eta);
+          const double PQ0 = x->P[0] - y->P[0], PQ1 = x->P[1] - y->P[1], PQ2 = x->P[2] - y->P[2];
+          const double inv_s = rd * rd;
+          const double T = zeta * eta * inv_s * fma(PQ0, PQ0, fma(PQ1, PQ1, PQ2 * PQ2));
+          int ti;
+          double xx, invT, rsqT;
+          rys_locate(T, a.rys_tcut_d, ti, xx, invT, rsqT);
+          const int od = j * NPD;
+          sd[od + 0] = xx;
+          sd[od + 1] = invT;
+          sd[od + 2] = rsqT;
+          sd[od + 3] = __longlong_as_double((long long)ti);
+          const double rz = eta * inv_s, re = zeta * inv_s;
+          const int o = j * GNPR;
+          sr[o + 0] = x->PA[0]; sr[o + 1] = x->PA[1]; sr[o + 2] = x->PA[2];
+          sr[o + 3] = y->PA[0]; sr[o + 4] = y->PA[1]; sr[o + 5] = y->PA[2];
+          sr[o + 6] = rz * PQ0; sr[o + 7] = rz * PQ1; sr[o + 8] = rz * PQ2;
+          sr[o + 9] = re * PQ0; sr[o + 10] = re * PQ1; sr[o + 11] = re * PQ2;
+          sr[o + 12] = 0.5 * inv_s;
+          sr[o + 13] = x->hz * rz;
+          sr[o + 14] = y->hz * re;
+          sr[o + 15] = x->E * y->E * rd;
+          sr[o + 16] = x->hz;
+          sr[o + 17] = y->hz;
+          sr[o + 18] = 2.0 * x->alpha;
+          sr[o + 19] = 2.0 * (zeta - x->alpha);
+          sr[o + 20] = 2.0 * y->alpha;
+        }
+      }
+      __syncwarp();
+      // b. roots, weights and the 2D tables per (primitive, root), or per (primitive, root,
+      //    axis) when that fills more of the team's lanes
+      if (TS > 1 && g.split3) {
+        for (int tk = tl; tk < bp * N * 3; tk += TS) {
+          const int jn = tk / 3, ax = tk - jn * 3;
+          const int j = jn / N, n = jn - (jn / N) * N;
+          if (j < nbt) {
+            const int od = j * NPD, o = j * GNPR;
+            double u, w;
+            rys_root(a.rys_coef, a.rys_au, a.rys_aw, N, (int)__double_as_longlong(sd[od + 3]), sd[od + 0],
+                     sd[od + 1], sd[od + 2], n, u, w);
+            const double B00 = u * sr[o + 12];
+            const double B10 = fma(-u, sr[o + 13], sr[o + 16]);
+            const double B01 = fma(-u, sr[o + 14], sr[o + 17]);
+            const double Cax = fma(-u, sr[o + 6 + ax], sr[o + 0 + ax]);
+            const double Cpx = fma(u, sr[o + 9 + ax], sr[o + 3 + ax]);
+            const double I00 = (ax == 2) ? w * sr[o + 15] : 1.0;
+            const int gt = S_2D + ((j * 6 + ax) * N + n) * nI;
+            rys_2d1<double>(sr, gt, Le2, Lf2, I00, Cax, Cpx, B00, B10, B01);
+            if (ax == 2) {
+              const double w1 = sr[o + 18], w2 = sr[o + 19], w3 = sr[o + 20];
+              for (int i = 0; i < nI; ++i) {
+                const double z = sr[gt + i];
+                sr[gt + N * nI + i] = w1 * z;
+                sr[gt + 2 * N * nI + i] = w2 * z;
+                sr[gt + 3 * N * nI + i] = w3 * z;
+              }
+            }
+          }
+        }
+      } else {
+        for (int tk = tl; tk < bp * N; tk += TS) {
+          const int j = tk / N, n = tk - (tk / N) * N;
+          if (j < nbt) {
+            const int od = j * NPD, o = j * GNPR;
+            double u, w;
+            rys_root(a.rys_coef, a.rys_au, a.rys_aw, N, (int)__double_as_longlong(sd[od + 3]), sd[od + 0],
+                     sd[od + 1], sd[od + 2], n, u, w);
+            const double B00 = u * sr[o + 12];
+            const double B10 = fma(-u, sr[o + 13], sr[o + 16]);
+            const double B01 = fma(-u, sr[o + 14], sr[o + 17]);
+            const double wt = w * sr[o + 15];
+            const double C[3] = {fma(-u, sr[o + 6], sr[o + 0]), fma(-u, sr[o + 7], sr[o + 1]),
+                                 fma(-u, sr[o + 8], sr[o + 2])};
+            const double Cp[3] = {fma(u, sr[o + 9], sr[o + 3]), fma(u, sr[o + 10], sr[o + 4]),
+                                  fma(u, sr[o + 11], sr[o + 5])};
+            const int g0 = S_2D + ((j * 6 + 0) * N + n) * nI;
+            const int og[3] = {g0, g0 + N * nI, g0 + 2 * N * nI};
+            rys_2d3<double>(sr, og, Le2, Lf2, wt, C, Cp, B00, B10, B01);
+            // the I_z table scaled by the primitive weights 2 alpha, 2 beta, 2 gamma
+            const double w1 = sr[o + 18], w2 = sr[o + 19], w3 = sr[o + 20];
+            for (int i = 0; i < nI; ++i) {
+              const double z = sr[og[2] + i];
+              sr[og[2] + N * nI + i] = w1 * z;
+              sr[og[2] + 2 * N * nI + i] = w2 * z;
+              sr[og[2] + 3 * N * nI + i] = w3 * z;
+            }
           }
         }
       }
+      __syncwarp();
+    };
+    auto assemble = [&](int nbt) {
+      // c. assembly and contraction in registers by lane programs: a slot that starts a
+      //    group forms the group's I_x I_y product, each value adds product x weighted I_z
+      for (int j = 0; j < bp; ++j) {
+        if (j < nbt) {
+          for (int n = 0; n < N; ++n) {
+            const int gx = S_2D + ((j * 6 + 0) * N + n) * nI;
+            const int gy = gx + N * nI;
+            const int gz = gy + N * nI;
+            double v = 0.0;
+#pragma unroll
+            for (int k = 0; k < GSLOTS; ++k) {
+              if (k < kcnt) {
+                const uint32_t p = (TS == 1) ? __ldg(g.outidx + o0 + k) : pkd[k];
+                if ((gm >> k) & 1u) v = sr[gx + (int)(p & 0xffu)] * sr[gy + (int)((p >> 8) & 0xffu)];
+                acc[k] = fma(v, sr[gz + (int)((p >> 16) & 0xfffu)], acc[k]);
+              }
+            }
+          }
+        }
+      }
+      __syncwarp();
+    };
+    const int nbatch = (maxq + bp - 1) / bp;        // uniform
+    if (g.npass > 1) {
+      for (int bi = 0; bi < nbatch; ++bi) {
+        const int q0 = bi * bp, nbt = min(bp, nq - q0);
+        batch_tables(q0, nbt);
+        for (int pass = 0; pass < g.npass; ++pass) {
+          begin_pass(pass, bi > 0);
+          assemble(nbt);
+          end_pass();
+        }
+      }
+    } else {
+      begin_pass(0, false);
+      for (int bi = 0; bi < nbatch; ++bi) {
+        const int q0 = bi * bp, nbt = min(bp, nq - q0);
+        batch_tables(q0, nbt);
+        assemble(nbt);
+      }
+      end_pass();
     }
+    __syncwarp();
 
     // ---- Gamma_J, Gamma_K of this quartet
     if (active) {

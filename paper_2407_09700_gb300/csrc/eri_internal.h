@@ -205,6 +205,7 @@ int erik_launch_class(int ts, int fp32, const struct KernelArgs* a, int grid, in
 // status in *rc) when one matches the class, team size and assembly path, else returns 0
 int erik_launch_class_spec(int ts, int xy, const struct KernelArgs* a, int grid, int smem_bytes, void* stream, int* rc);
 int erik_class_spec_prepare(void);
+int erik_class_spec_available(int ts, int la, int lb, int lc, int ld);
 int erik_upload_cart_tables_spec(void);
 int erik_launch_compact(const struct KernelArgs* a, unsigned* tlist, unsigned long long cap,
                         unsigned long long* counts, unsigned* tiles, int mixed, void* stream);

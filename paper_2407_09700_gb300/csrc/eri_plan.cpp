@@ -1625,6 +1625,7 @@ eri_status eri_launch_records(eri_plan* p, eri_launch_record* out, int cap, int*
     r.fp32 = f;
     r.specialised = p->last_launch_small[i];
     r.shared_products = (!f && !r.specialised && c.xy) ? 1 : 0;
+    r.compiled_class = (!f && !r.specialised && erik_class_spec_available(r.team_size, c.la, c.lb, c.lc, c.ld)) ? 1 : 0;
   }
   return ERI_OK;
 }

@@ -295,8 +295,8 @@ def make_jobs(requests, natm_cap: Optional[int] = None) -> List[Job]:
 
 
 def main():
-    """Served-workload benchmark: continuous batching (mixed precision) against sequential
-    FP64 on the same requests; prints one JSON line."""
+    """Served-workload benchmark: continuous batching in mixed precision and in FP64 against
+    sequential FP64 on the same requests; prints one JSON line."""
     import argparse
     import json
 
@@ -312,20 +312,33 @@ def main():
     ap.add_argument("--slots", type=int, default=32)
     ap.add_argument("--hbm-gb", type=float, default=64.0)
     ap.add_argument("--no-sequential", action="store_true")
+    ap.add_argument("--no-batched-fp64", action="store_true")
     args = ap.parse_args()
     build()
     reqs = config_served_requests(seed=args.seed, nreq=args.requests, mean_interarrival_s=args.mean_interarrival,
                                   natm_range=(args.natm_min, args.natm_max))
     # warm the kernels and the allocator on one small request
-    warm = make_jobs(reqs[:1], natm_cap=5)
-    Server().run(warm)
-    served = Server(hbm_budget=int(args.hbm_gb * (1 << 30)), max_slots=args.slots).run(make_jobs(reqs))
+    Server().run(make_jobs(reqs[:1], natm_cap=5))
+
+    def arm(fn):
+        jobs = make_jobs(reqs)
+        out = fn(jobs)
+        scf = [j for j in jobs if j.kind == "scf"]
+        out["scf_jobs"] = len(scf)
+        out["scf_converged"] = sum(1 for j in scf if j.result.get("converged"))
+        out["scf_iterations_mean"] = float(np.mean([j.iters for j in scf])) if scf else 0.0
+        return out
+
+    budget = int(args.hbm_gb * (1 << 30))
     out = {"workload": f"{args.requests} requests, exponential inter-arrival mean {args.mean_interarrival * 1e3:.0f} ms, "
-                       f"atoms log-uniform [{args.natm_min}, {args.natm_max}], 30% RHF to 1e-8 Ha, 70% single J/K; "
-                       "heavy/light 3s2p1d/2s1p recipe",
-           "served_mixed": served}
+                       f"atoms log-uniform [{args.natm_min}, {args.natm_max}], 30% RHF to 1e-8 Ha (at most 100 "
+                       "iterations), 70% single J/K; heavy/light 3s2p1d/2s1p recipe",
+           "batched_mixed": arm(lambda jobs: Server(hbm_budget=budget, max_slots=args.slots).run(jobs))}
+    if not args.no_batched_fp64:
+        out["batched_fp64"] = arm(lambda jobs: Server(precision=ERI_FP64, hbm_budget=budget,
+                                                      max_slots=args.slots).run(jobs))
     if not args.no_sequential:
-        out["sequential_fp64"] = run_sequential(make_jobs(reqs))
+        out["sequential_fp64"] = arm(run_sequential)
     print(json.dumps(out))
 
 
