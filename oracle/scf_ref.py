@@ -3,7 +3,10 @@ integrals (test infrastructure only).
 
 Textbook closed-shell SCF: D = 2 C_occ C_occ^T, F = H + J - K/2,
 E = tr(D (H + F))/2 + E_nuc, core-Hamiltonian guess, canonical orthogonalisation
-(overlap eigenvalues below 1e-8 dropped), DIIS on FDS - SDF with 8 vectors.
+(overlap eigenvalues below 1e-8 dropped), DIIS on FDS - SDF with 8 vectors.  Optional
+damping of the first new densities (D <- (1 - damp) D_new + damp D_old for damp_cycles
+iterations) and DIIS from iteration diis_start on (PySCF's damp / diis_start_cycle);
+the defaults (0, 0, 1) are plain DIIS from the second iteration.
 """
 
 from __future__ import annotations
@@ -14,7 +17,8 @@ from . import oracle as _orc
 from .onee import nuclear_repulsion, one_electron
 
 
-def rhf(mol, charge=0, max_iter=50, conv_tol=1e-10, fixed_iters=None, diis_space=8, onee=None, jk=None):
+def rhf(mol, charge=0, max_iter=50, conv_tol=1e-10, fixed_iters=None, diis_space=8, onee=None, jk=None,
+        damp=0.0, damp_cycles=0, diis_start=1):
     S, T, V = onee if onee is not None else one_electron(mol)
     H = T + V
     enuc = nuclear_repulsion(mol.coords, mol.charges)
@@ -52,7 +56,7 @@ def rhf(mol, charge=0, max_iter=50, conv_tol=1e-10, fixed_iters=None, diis_space
         if len(fs) > diis_space:
             fs.pop(0)
             es.pop(0)
-        if len(fs) >= 2 and np.abs(err).max() > 1e-13:
+        if it - 1 >= diis_start and len(fs) >= 2 and np.abs(err).max() > 1e-13:
             n = len(fs)
             B = -np.ones((n + 1, n + 1))
             B[n, n] = 0.0
@@ -63,7 +67,8 @@ def rhf(mol, charge=0, max_iter=50, conv_tol=1e-10, fixed_iters=None, diis_space
             rhs[n] = -1.0
             c = np.linalg.solve(B, rhs)
             F = sum(c[i] * fs[i] for i in range(n))
-        D = density(F)
+        D_new = density(F)
+        D = (1.0 - damp) * D_new + damp * D if it - 1 < damp_cycles else D_new
         if fixed_iters is None and e_old is not None and abs(E - e_old) < conv_tol:
             converged = True
             break

@@ -10,7 +10,11 @@ library's host routine (the paper also computes them on the CPU, Sec. 4).
 
 Conventions (the paper does not print PySCF's): core-Hamiltonian guess,
 canonical orthogonalisation dropping overlap eigenvalues below 1e-8, DIIS with 8
-vectors starting at the second iteration.  With incremental = True (PySCF's direct-SCF
+vectors.  The defaults damp the first three new densities (D <- (D_new + D_old) / 2) and
+extrapolate with DIIS from the fourth iteration on (PySCF's `damp` and
+`diis_start_cycle`); damp = 0, diis_start = 1 gives plain DIIS from the second iteration.
+On the lattice molecules of the SCF recipe plain DIIS from a core guess stalls in an
+excited solution, the damped start converges.  With incremental = True (PySCF's direct-SCF
 scheme, on which the paper's GPU4PySCF builds) every build after the first evaluates J
 and K of the density change D_n - D_{n-1} and adds them to the previous J and K; the
 screening of Eqs. 7-9 then uses max|D_n - D_{n-1}|, which shrinks as the SCF converges.
@@ -51,7 +55,8 @@ class SCFResult:
 class RHF:
     def __init__(self, mol, charge: Optional[int] = None, precision: int = ERI_FP64, mixed_thresh: float = 1e-4,
                  tau: Optional[float] = None, lindep: float = 1e-8, plan: Optional[Plan] = None, stream=None,
-                 device: str = "cuda", incremental: bool = False):
+                 device: str = "cuda", incremental: bool = False, damp: float = 0.5, damp_cycles: int = 3,
+                 diis_start: int = 3):
         """device: where the matrices live ("cuda"; the step-wise start / update interface also
         runs on "cpu" with J and K supplied by the caller).  incremental: build J, K of the
         density change after the first iteration (see the module docstring)."""
@@ -59,6 +64,7 @@ class RHF:
         self.torch = torch
         self.mol = mol
         self.incremental = bool(incremental)
+        self.damp, self.damp_cycles, self.diis_start = float(damp), int(damp_cycles), int(diis_start)
         if charge is None:
             charge = int(getattr(mol, "net_charge", 0))
         nel = int(round(float(np.sum(mol.charges)))) - charge
@@ -93,6 +99,7 @@ class RHF:
         self.fs, self.es, self.energies = [], [], []
         self.e_old = None
         self.converged = False
+        self.cycle = 0
         self.J_acc = self.K_acc = self.D_acc = None
         if D0 is None:
             self.D, self.mo_e = self._density(self.H)
@@ -126,7 +133,7 @@ class RHF:
         if len(self.fs) > self.diis_space:
             self.fs.pop(0)
             self.es.pop(0)
-        if len(self.fs) >= 2:
+        if self.cycle >= self.diis_start and len(self.fs) >= 2:
             # B_ij = <e_i, e_j> for all stored error vectors at once; the extrapolation is skipped
             # (coefficients of the newest Fock matrix) once the error is below 1e-13
             n = len(self.fs)
@@ -142,7 +149,11 @@ class RHF:
             use = (err.abs().max() > 1e-13) & (info == 0) & torch.isfinite(sol).all()
             c = torch.where(use, torch.nan_to_num(sol[:n]), last)
             F = torch.einsum("i,ijk->jk", c, torch.stack(self.fs))
-        self.D, self.mo_e = self._density(F)
+        D_new, self.mo_e = self._density(F)
+        if self.cycle < self.damp_cycles and self.damp > 0.0:
+            D_new = (1.0 - self.damp) * D_new + self.damp * D
+        self.D = D_new
+        self.cycle += 1
         energy = float(e_dev) + self.enuc
         self.energies.append(energy)
         if conv_tol is not None and self.e_old is not None and abs(energy - self.e_old) < conv_tol:

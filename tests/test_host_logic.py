@@ -215,16 +215,17 @@ def test_rhf_driver_steps_match_the_oracle_rhf_on_cpu():
             K = int(rng.integers(1, 4))
             shells.append((a, l, np.sort(rng.uniform(0.2, 4.0, K))[::-1], rng.uniform(0.2, 1.0, K)))
     m = custom_molecule(coords, shells, charges=[6.0, 1.0, 1.0])
-    drv = RHF(m, plan=object(), device="cpu")
-    D = drv.start()
-    energies = []
-    for _ in range(10):
-        J, K, _ = oracle.jk(m, D=D.numpy()[None])
-        e, _ = drv.update(torch.from_numpy(J[0]), torch.from_numpy(K[0]), None)
-        energies.append(e)
-        D = drv.D
-    _, ref_hist, _ = scf_ref.rhf(m, fixed_iters=10)
-    np.testing.assert_allclose(energies, ref_hist, atol=1e-8, rtol=0)
+    for scheme in (dict(damp=0.5, damp_cycles=3, diis_start=3), dict(damp=0.0, damp_cycles=0, diis_start=1)):
+        drv = RHF(m, plan=object(), device="cpu", **scheme)
+        D = drv.start()
+        energies = []
+        for _ in range(10):
+            J, K, _ = oracle.jk(m, D=D.numpy()[None])
+            e, _ = drv.update(torch.from_numpy(J[0]), torch.from_numpy(K[0]), None)
+            energies.append(e)
+            D = drv.D
+        _, ref_hist, _ = scf_ref.rhf(m, fixed_iters=10, **scheme)
+        np.testing.assert_allclose(energies, ref_hist, atol=1e-8, rtol=0)
 
 
 def test_reference_arm_under_two_ranks_prints_one_line():
