@@ -10,11 +10,11 @@ library's host routine (the paper also computes them on the CPU, Sec. 4).
 
 Conventions (the paper does not print PySCF's): core-Hamiltonian guess,
 canonical orthogonalisation dropping overlap eigenvalues below 1e-8, DIIS with 8
-vectors.  The defaults damp the first three new densities (D <- (D_new + D_old) / 2) and
-extrapolate with DIIS from the fourth iteration on (PySCF's `damp` and
-`diis_start_cycle`); damp = 0, diis_start = 1 gives plain DIIS from the second iteration.
-On the lattice molecules of the SCF recipe plain DIIS from a core guess stalls in an
-excited solution, the damped start converges.  With incremental = True (PySCF's direct-SCF
+vectors from the second iteration.  Optionally the first damp_cycles new densities are
+damped (D <- (1 - damp) D_new + damp D_old) and DIIS starts later (PySCF's `damp` and
+`diis_start_cycle`): on the 8-atom lattice molecule of the SCF recipe that start
+converges where plain DIIS stalls, on the 120-atom one it diverged, so plain DIIS is the
+default.  With incremental = True (PySCF's direct-SCF
 scheme, on which the paper's GPU4PySCF builds) every build after the first evaluates J
 and K of the density change D_n - D_{n-1} and adds them to the previous J and K; the
 screening of Eqs. 7-9 then uses max|D_n - D_{n-1}|, which shrinks as the SCF converges.
@@ -55,8 +55,8 @@ class SCFResult:
 class RHF:
     def __init__(self, mol, charge: Optional[int] = None, precision: int = ERI_FP64, mixed_thresh: float = 1e-4,
                  tau: Optional[float] = None, lindep: float = 1e-8, plan: Optional[Plan] = None, stream=None,
-                 device: str = "cuda", incremental: bool = False, damp: float = 0.5, damp_cycles: int = 3,
-                 diis_start: int = 3):
+                 device: str = "cuda", incremental: bool = False, damp: float = 0.0, damp_cycles: int = 0,
+                 diis_start: int = 1):
         """device: where the matrices live ("cuda"; the step-wise start / update interface also
         runs on "cpu" with J and K supplied by the caller).  incremental: build J, K of the
         density change after the first iteration (see the module docstring)."""

@@ -51,13 +51,13 @@ def test_heh_plus_sto3g_on_gpu():
 
 def test_rhf_matches_oracle_rhf():
     m = _small(1)
-    # the driver's default start (three damped densities, DIIS from the fourth iteration) and
-    # plain DIIS from the second iteration, each against the oracle's RHF with the same scheme
-    ref_E, ref_hist, _ = scf_ref.rhf(m, fixed_iters=12, damp=0.5, damp_cycles=3, diis_start=3)
+    # plain DIIS from the second iteration (the default) and a damped start (three damped
+    # densities, DIIS from the fourth iteration), each against the oracle's RHF with that scheme
+    ref_E, ref_hist, _ = scf_ref.rhf(m, fixed_iters=12)
     r = RHF(m).kernel(fixed_iters=12)
     np.testing.assert_allclose(r.energies, ref_hist, atol=1e-8, rtol=0)
-    ref_E, ref_hist, _ = scf_ref.rhf(m, fixed_iters=12)
-    r = RHF(m, damp=0.0, damp_cycles=0, diis_start=1).kernel(fixed_iters=12)
+    ref_E, ref_hist, _ = scf_ref.rhf(m, fixed_iters=12, damp=0.5, damp_cycles=3, diis_start=3)
+    r = RHF(m, damp=0.5, damp_cycles=3, diis_start=3).kernel(fixed_iters=12)
     np.testing.assert_allclose(r.energies, ref_hist, atol=1e-8, rtol=0)
 
 
