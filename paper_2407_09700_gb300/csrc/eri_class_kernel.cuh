@@ -84,6 +84,7 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : ((sizeof(R) == 4 && !XY) ?
   double* E0 = scr;                                  // [ne][nf] contracted [e0|f0]
   double* bufA = scr + c.nout;
   double* bufB = bufA + c.hrr_doubles;
+  double* part = scr + c.part_off;                   // slot-ordered partial sums (several passes)
 
   unsigned long long cnt_q = 0, cnt_p = 0;
 
@@ -171,7 +172,7 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : ((sizeof(R) == 4 && !XY) ?
       const uint32_t p = (TS == 1) ? __ldg(outidx + o0 + k) : pkd[k];
       return XY || !(p >> 31);
     };
-    auto begin_pass = [&](int pass, bool from_e0) {
+    auto begin_pass = [&](int pass, bool from_part) {
       o0 = pass * TS * GSLOTS;
       kcnt = min(GSLOTS, (nslot - o0 + TS - 1) / TS);     // uniform
 #pragma unroll
@@ -181,10 +182,12 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : ((sizeof(R) == 4 && !XY) ?
         if (TS > 1) pkd[k] = (o < nslot) ? __ldg(outidx + o) : (1u << 31);
         acc[k] = R(0);
       }
-      if (from_e0 && active) {
+      if (from_part && active) {
 #pragma unroll
-        for (int k = 0; k < GSLOTS; ++k)
-          if (slot_valid(k)) acc[k] = (R)E0[(int)__ldg(dsttab + o0 + k * TS + tl)];
+        for (int k = 0; k < GSLOTS; ++k) {
+          const int o = o0 + k * TS + tl;
+          if (k < kcnt && o < nslot) acc[k] = (R)part[o];
+        }
       }
       gm = XY ? 0u : __ldg(c.gmask + pass);           // group starts (uniform)
       if (XY) {
@@ -197,12 +200,21 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : ((sizeof(R) == 4 && !XY) ?
         }
       }
     };
-    // ---- contracted values of this pass -> team scratch ([e][f] order)
-    auto end_pass = [&]() {
+    // ---- contracted values of this pass -> team scratch: [e][f] order after the last batch,
+    //      else the partial sums in slot order (consecutive lanes, consecutive addresses)
+    auto end_pass = [&](bool last) {
       if (active) {
+        if (last) {
 #pragma unroll
-        for (int k = 0; k < GSLOTS; ++k)
-          if (slot_valid(k)) E0[(int)__ldg(dsttab + o0 + k * TS + tl)] = (double)acc[k];
+          for (int k = 0; k < GSLOTS; ++k)
+            if (slot_valid(k)) E0[(int)__ldg(dsttab + o0 + k * TS + tl)] = (double)acc[k];
+        } else {
+#pragma unroll
+          for (int k = 0; k < GSLOTS; ++k) {
+            const int o = o0 + k * TS + tl;
+            if (k < kcnt && o < nslot) part[o] = (double)acc[k];
+          }
+        }
       }
     };
     // ---- a. and b. of one batch of primitive quartets (every lane of the warp calls it)
@@ -370,7 +382,7 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : ((sizeof(R) == 4 && !XY) ?
         for (int pass = 0; pass < npass; ++pass) {
           begin_pass(pass, bi > 0);
           assemble(nbt);
-          end_pass();
+          end_pass(bi == nbatch - 1);
         }
       }
     } else {
@@ -381,7 +393,7 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : ((sizeof(R) == 4 && !XY) ?
           batch_tables(q0, nbt);
           assemble(nbt);
         }
-        end_pass();
+        end_pass(true);
       }
     }
     __syncwarp();

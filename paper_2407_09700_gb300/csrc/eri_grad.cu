@@ -140,6 +140,7 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : 2)) eri_grad_kernel(const 
   double* GK = GJ + nabcd;
   double* bufA = scr + g.hrr_off;
   double* bufB = bufA + g.hrr_doubles;
+  double* part = scr + g.part_off;     // slot-ordered partial sums between batches (several passes)
   const int nbase[4] = {g.na, g.nb, g.nc, g.nd};
 
   unsigned long long cnt_q = 0, cnt_p = 0;
@@ -186,7 +187,7 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : 2)) eri_grad_kernel(const 
       const uint32_t p = (TS == 1) ? __ldg(g.outidx + o0 + k) : pkd[k];
       return !(p >> 31);
     };
-    auto begin_pass = [&](int pass, bool from_scr) {
+    auto begin_pass = [&](int pass, bool from_part) {
       o0 = pass * TS * GSLOTS;
       kcnt = min(GSLOTS, (g.nslot - o0 + TS - 1) / TS);
 #pragma unroll
@@ -195,18 +196,28 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : 2)) eri_grad_kernel(const 
         if (TS > 1) pkd[k] = (o < g.nslot) ? __ldg(g.outidx + o) : (1u << 31);
         acc[k] = 0.0;
       }
-      if (from_scr && active) {
+      if (from_part && active) {
 #pragma unroll
-        for (int k = 0; k < GSLOTS; ++k)
-          if (slot_valid(k)) acc[k] = scr[__ldg(g.dst + o0 + k * TS + tl)];
+        for (int k = 0; k < GSLOTS; ++k) {
+          const int o = o0 + k * TS + tl;
+          if (k < kcnt && o < g.nslot) acc[k] = part[o];
+        }
       }
       gm = __ldg(g.gmask + pass);
     };
-    auto end_pass = [&]() {
+    auto end_pass = [&](bool last) {
       if (active) {
+        if (last) {
 #pragma unroll
-        for (int k = 0; k < GSLOTS; ++k)
-          if (slot_valid(k)) scr[__ldg(g.dst + o0 + k * TS + tl)] = acc[k];
+          for (int k = 0; k < GSLOTS; ++k)
+            if (slot_valid(k)) scr[__ldg(g.dst + o0 + k * TS + tl)] = acc[k];
+        } else {
+#pragma unroll
+          for (int k = 0; k < GSLOTS; ++k) {
+            const int o = o0 + k * TS + tl;
+            if (k < kcnt && o < g.nslot) part[o] = acc[k];
+          }
+        }
       }
     };
     auto batch_tables = [&](int q0, int nbt) {
@@ -340,7 +351,7 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : 2)) eri_grad_kernel(const 
         for (int pass = 0; pass < g.npass; ++pass) {
           begin_pass(pass, bi > 0);
           assemble(nbt);
-          end_pass();
+          end_pass(bi == nbatch - 1);
         }
       }
     } else {
@@ -350,7 +361,7 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : 2)) eri_grad_kernel(const 
         batch_tables(q0, nbt);
         assemble(nbt);
       }
-      end_pass();
+      end_pass(true);
     }
     __syncwarp();
 

@@ -59,6 +59,8 @@ struct ClassDesc {
   int team_doubles_f32;  // shared-memory doubles per team (FP32 recurrences)
   int hrr_doubles;       // size of one HRR ping-pong buffer (doubles)
   long long scratch_per_team;  // global scratch doubles per team
+  long long part_off;    // FP64 classes with several passes: offset of the slot-ordered partial sums
+                         // carried between primitive batches (0 when a class has one pass)
   int split3, split3_xy; // 1: the root phase runs (primitive, root, axis) items (batch bp / bp_xy)
   // Assembly of Eq. 1 by lane programs (every FP32 launch; FP64 launches with xy = 0): the
   // values sharing an I_x I_y product form groups; every lane of a team runs the same
@@ -180,6 +182,7 @@ struct GradDesc {
   int gam_off;                                // Gamma_J, Gamma_K: 2 * na nb nc nd doubles
   int hrr_off, hrr_doubles;                   // two HRR ping-pong buffers
   long long scratch_per_team;
+  long long part_off;                         // slot-ordered partial sums between batches (npass > 1)
   const uint32_t* outidx;                     // [nslot] slot words
   const uint32_t* dst;                        // [nslot] position in the concatenated sets
   const uint32_t* gmask;                      // [npass] group starts

@@ -133,13 +133,17 @@ ClassTune class_tune(int la, int lb, int lc, int ld) {
     }
   }
   ClassTune t;
-  // team sizes measured fastest on GB300 for the s/p/d classes of contracted 6-31G(d)-like
-  // shells (per-class CUDA-event times of the FP64 build, 1/2/4/8/32 lanes compared; 1 =
-  // the specialised one-lane kernel)
-  static const int measured[][5] = {{2, 1, 1, 0, 1}, {2, 0, 1, 1, 1}, {2, 0, 2, 0, 1}, {2, 2, 1, 0, 4},
-                                    {1, 1, 1, 1, 4}, {2, 2, 2, 1, 8}};
+  // team sizes and assembly paths measured fastest on GB300 for the s/p/d classes of
+  // contracted 6-31G(d)-like shells (per-class CUDA-event times of the FP64 build, 1/2/4/8/32
+  // lanes compared, 1 = the specialised one-lane kernel; products path -1 = the automatic
+  // rule, 0 = lane programs: (dd|dp) 981 -> 878 ms on the 30-atom build)
+  static const int measured[][6] = {{2, 1, 1, 0, 1, -1}, {2, 0, 1, 1, 1, -1}, {2, 0, 2, 0, 1, -1},
+                                    {2, 2, 1, 0, 4, -1}, {1, 1, 1, 1, 4, -1}, {2, 2, 2, 1, 8, 0}};
   for (const auto& m : measured)
-    if (m[0] == la && m[1] == lb && m[2] == lc && m[3] == ld) t.ts = m[4];
+    if (m[0] == la && m[1] == lb && m[2] == lc && m[3] == ld) {
+      t.ts = m[4];
+      t.xy = m[5];
+    }
   for (const auto& v : table)
     if (v[0] == la && v[1] == lb && v[2] == lc && v[3] == ld) {
       if (v[4] == 1 || v[4] == 2 || v[4] == 4 || v[4] == 8 || v[4] == 32) t.ts = v[4];
@@ -389,6 +393,11 @@ void make_class(int la, int lb, int lc, int ld, ClassDesc* c, int* ts, std::vect
   }
   c->hrr_doubles = (int)((m + 1) & ~1LL);
   c->scratch_per_team = ((long long)c->nout + 1) / 2 * 2 + 2LL * c->hrr_doubles;
+  // FP64 classes with several output passes carry each pass's partial sums from batch to
+  // batch in slot order (a warp's loads and stores of them are contiguous)
+  const bool multi = c->npass > 1 || (c->xy && c->xy_npass > 1);
+  c->part_off = multi ? c->scratch_per_team : 0;
+  if (multi) c->scratch_per_team += ((long long)std::max(c->nslot, c->nout) + 1) / 2 * 2;
 }
 
 // Fill the static part of a gradient class descriptor (Sec. 4): the four contracted sets,
@@ -478,6 +487,8 @@ void make_grad_class(int la, int lb, int lc, int ld, GradDesc* g, int* ts, std::
   if (lc > 0) seq(la, lb, lc - 1, ld);
   g->hrr_doubles = (int)((m + 1) & ~1LL);
   g->scratch_per_team = (long long)g->hrr_off + 2LL * g->hrr_doubles;
+  g->part_off = g->npass > 1 ? g->scratch_per_team : 0;
+  if (g->npass > 1) g->scratch_per_team += ((long long)g->nslot + 1) / 2 * 2;
   g->outidx = nullptr;
 }
 
