@@ -41,14 +41,15 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : ((sizeof(R) == 4 && !XY) ?
   constexpr bool SPEC = CLS >= 0;
   constexpr int SLe = SPEC ? CLS / 1000 + (CLS / 100) % 10 : 0, SLf = SPEC ? (CLS / 10) % 10 + CLS % 10 : 0;
   constexpr int SN = (SLe + SLf) / 2 + 1, SnI = (SLe + 1) * (SLf + 1);
-  const int N = SPEC ? SN : c.nroots, nI = SPEC ? SnI : c.nI, Le = SPEC ? SLe : c.Le, Lf = SPEC ? SLf : c.Lf;
+  constexpr int SnIs = TS > 1 ? (SnI | 1) : SnI;
+  const int N = SPEC ? SN : c.nroots, nIs = SPEC ? SnIs : c.nIs, Le = SPEC ? SLe : c.Le, Lf = SPEC ? SLf : c.Lf;
   const int bp = XY ? c.bp_xy : c.bp;
   const int npass = XY ? c.xy_npass : c.npass;
   const int nslot = XY ? c.nout : c.nslot;
   const uint32_t* outidx = XY ? c.xy_outidx : c.outidx;
   const uint32_t* dsttab = XY ? c.xy_dst : c.dst;
 
-  // team region: [bp][NPD] doubles, then [bp][NPR] R, then [bp][3][N][nI] R
+  // team region: [bp][NPD] doubles, then [bp][NPR] R, then [bp][3][N] tables of nI R, nIs apart
   Smem<double> sd;
   Smem<R> sr;
   if (TS == 1) {
@@ -77,7 +78,7 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : ((sizeof(R) == 4 && !XY) ?
     __syncwarp();
   }
   const int S_2D = bp * NPR;                         // R offset of the 2D tables
-  R* xyb = XY ? &sr[S_2D + bp * 3 * N * nI] : nullptr;   // product buffers (xy classes)
+  R* xyb = XY ? &sr[S_2D + bp * 3 * N * nIs] : nullptr;   // product buffers (xy classes)
   // contracted [e0|f0] and the transfer relations are FP64 in both paths: the FP32 path
   // hands its contracted values over before the transfer, whose cancellations grow with |A-B|
   double* scr = a.scratch + gteam * c.scratch_per_team;
@@ -279,7 +280,7 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : ((sizeof(R) == 4 && !XY) ?
             const R Cax = fma(-u, sr[o + 6 + ax], sr[o + 0 + ax]);
             const R Cpx = fma(u, sr[o + 9 + ax], sr[o + 3 + ax]);
             const R I00 = (ax == 2) ? (R)wd * sr[o + 15] : R(1);
-            rys_2d1<R>(sr, S_2D + ((j * 3 + ax) * N + n) * nI, Le, Lf, I00, Cax, Cpx, B00, B10, B01);
+            rys_2d1<R>(sr, S_2D + ((j * 3 + ax) * N + n) * nIs, Le, Lf, I00, Cax, Cpx, B00, B10, B01);
           }
         }
       } else {
@@ -299,8 +300,8 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : ((sizeof(R) == 4 && !XY) ?
                             fma(-u, sr[o + 8], sr[o + 2])};
             const R Cp[3] = {fma(u, sr[o + 9], sr[o + 3]), fma(u, sr[o + 10], sr[o + 4]),
                              fma(u, sr[o + 11], sr[o + 5])};
-            const int g0 = S_2D + ((j * 3 + 0) * N + n) * nI;
-            const int og[3] = {g0, g0 + N * nI, g0 + 2 * N * nI};
+            const int g0 = S_2D + ((j * 3 + 0) * N + n) * nIs;
+            const int og[3] = {g0, g0 + N * nIs, g0 + 2 * N * nIs};
             rys_2d3<R>(sr, og, Le, Lf, wt, C, Cp, B00, B10, B01);
           }
         }
@@ -319,8 +320,8 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : ((sizeof(R) == 4 && !XY) ?
         const int nsteps = warp_max(nbt) * N;
         auto form = [&](int st) {
           const int jj = st / N, nn = st - (st / N) * N;
-          const int gx = S_2D + ((jj * 3 + 0) * N + nn) * nI;
-          const int gy = gx + N * nI;
+          const int gx = S_2D + ((jj * 3 + 0) * N + nn) * nIs;
+          const int gy = gx + N * nIs;
           R* buf = xyb + (st & 1) * c.xymax;
 #pragma unroll
           for (int i = 0; i < XQ; ++i) {
@@ -338,7 +339,7 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : ((sizeof(R) == 4 && !XY) ?
           if (st + 1 < nsteps) form(st + 1);
           const int jj = st / N, nn = st - (st / N) * N;
           const bool jv = jj < nbt;
-          const int gz = S_2D + ((jj * 3 + 2) * N + nn) * nI;
+          const int gz = S_2D + ((jj * 3 + 2) * N + nn) * nIs;
           const R* buf = xyb + (st & 1) * c.xymax;
 #pragma unroll
           for (int k = 0; k < GSLOTS; ++k) {
@@ -356,9 +357,9 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : ((sizeof(R) == 4 && !XY) ?
         for (int j = 0; j < bp; ++j) {
           if (j < nbt) {
             for (int n = 0; n < N; ++n) {
-              const int gx = S_2D + ((j * 3 + 0) * N + n) * nI;
-              const int gy = gx + N * nI;
-              const int gz = gy + N * nI;
+              const int gx = S_2D + ((j * 3 + 0) * N + n) * nIs;
+              const int gy = gx + N * nIs;
+              const int gz = gy + N * nIs;
               R v = R(0);
 #pragma unroll
               for (int k = 0; k < GSLOTS; ++k) {

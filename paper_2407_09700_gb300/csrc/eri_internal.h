@@ -49,6 +49,7 @@ struct ClassDesc {
   int nroots;            // floor((la+lb+lc+ld)/2) + 1
   int Le, Lf;            // la + lb, lc + ld
   int nI;                // (Le+1)(Lf+1) 2D-integral entries per axis and root
+  int nIs;               // shared-memory stride of one such table: nI, odd in team kernels
   int ne, nf;            // Cartesian e with la <= |e| <= Le, f with lc <= |f| <= Lf
   int nout;              // ne * nf contracted [e0|f0] values
   int na, nb, nc, nd;    // shell sizes

@@ -107,6 +107,18 @@ int choose_ts(int nout) {
 // so two blocks fit on an SM.
 int team_budget(int ts) { return ts == 2 ? 192 : ts == 4 ? 384 : ts == 8 ? 768 : 3072; }
 
+// Shared-memory stride between the team regions of a block.  With TS lanes per team, the
+// 32 / TS teams of a warp read the same table entries at the same time; a stride of TS
+// doubles modulo 16 (FP64 tables) or of TS/2 doubles modulo 16 (FP32 tables, TS floats
+// modulo 32) puts the teams of a half-warp on disjoint windows of TS banks (pairs of banks
+// for doubles), so their reads of a slot's entries do not collide as long as a team's own
+// entries lie in distinct bank windows.
+int team_stride(int doubles, int ts, bool f32) {
+  if (ts <= 1 || ts >= 16) return doubles;
+  const int r = f32 ? ts / 2 : ts;
+  return doubles + ((r - doubles % 16) % 16 + 16) % 16;
+}
+
 // Per-class overrides of the team size, the products path and the staging of pair records:
 // "la lb lc ld ts xy [stage]" entries separated by ';' in ERI_CLASS_CONFIG (xy -1 = automatic;
 // stage 1 = bulk-copy staging, where a kernel compiled for the class has it), read once per
@@ -311,17 +323,14 @@ void make_class(int la, int lb, int lc, int ld, ClassDesc* c, int* ts, std::vect
     idx->insert(idx->end(), gm.begin(), gm.end());
   }
   // per primitive quartet: 4 doubles (table lookup) + 18 recurrence-type scalars + three 2D tables
-  const int per_prim = 4 + 18 + 3 * c->nroots * c->nI;
+  // the tables of one (primitive, root, axis) lie nIs apart, odd in team kernels: the lanes
+  // of a team building different tables then write distinct banks
+  c->nIs = (T > 1) ? (c->nI | 1) : c->nI;
+  const int per_prim = 4 + 18 + 3 * c->nroots * c->nIs;
   c->bp = (T == 1) ? 1 : std::max(1, std::min(32, team_budget(T) / per_prim));
-  c->team_doubles = c->bp * per_prim;
-  c->team_doubles_f32 = c->bp * 4 + (c->bp * (18 + 3 * c->nroots * c->nI) + 1) / 2;
+  c->team_doubles = team_stride(c->bp * per_prim, T, false);
+  c->team_doubles_f32 = team_stride(c->bp * 4 + (c->bp * (18 + 3 * c->nroots * c->nIs) + 1) / 2, T, true);
   c->split3 = choose_split3(T, c->bp, c->nroots, c->nI, 0);
-  // Team regions of a block start an odd number of doubles apart, so the teams of a warp
-  // reading the same table entry hit distinct shared-memory banks.
-  if (T > 1) {
-    c->team_doubles |= 1;
-    c->team_doubles_f32 |= 1;
-  }
 
   // ---- shared products path (FP64 launches of the classes where it measured faster):
   // values ordered by their product; per pass the first product and the count.
@@ -360,7 +369,7 @@ void make_class(int la, int lb, int lc, int ld, ClassDesc* c, int* ts, std::vect
       c->xysum_xy = xysum;
       c->bp_xy = bp_on;
       c->split3_xy = choose_split3(T, bp_on, c->nroots, c->nI, 0);
-      c->team_doubles_xy = (bp_on * per_prim + 2 * xymax) | 1;
+      c->team_doubles_xy = team_stride(bp_on * per_prim + 2 * xymax, T, false);
       std::vector<uint32_t> outi(c->nout), dst(c->nout);
       for (int p = 0; p < xnp; ++p) {
         const int o0 = p * per_pass, o1 = std::min(c->nout, o0 + per_pass) - 1;
@@ -464,8 +473,7 @@ void make_grad_class(int la, int lb, int lc, int ld, GradDesc* g, int* ts, std::
   } else {
     g->bp = std::max(1, std::min(32, team_budget(*ts) / per_prim));
   }
-  g->team_doubles = g->bp * per_prim;
-  if (*ts > 1) g->team_doubles |= 1;      // odd team stride: distinct banks across teams
+  g->team_doubles = team_stride(g->bp * per_prim, *ts, false);
   g->split3 = choose_split3(*ts, g->bp, g->nroots, g->nI, 3 * g->nI);
   const int nabcd = g->na * g->nb * g->nc * g->nd;
   g->gam_off = (off + 1) & ~1;
