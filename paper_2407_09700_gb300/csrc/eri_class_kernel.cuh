@@ -399,7 +399,10 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : ((sizeof(R) == 4 && !XY) ?
     }
     __syncwarp();
 
-    finish_quartet<TS, double>(a, tc, c, E0, bufA, bufB, tl, active, AB, CD, bra, ket, ib, ik, task);
+    // the team's shared region is free here: team kernels digest from it
+    finish_quartet<TS, double>(a, tc, c, E0, bufA, bufB, tl, active, AB, CD, bra, ket, ib, ik, task,
+                               TS > 1 ? sd.base : nullptr,
+                               XY ? c.team_doubles_xy : (sizeof(R) == 8 ? c.team_doubles : c.team_doubles_f32));
     __syncwarp();
   }
   // ---- counters: one atomic pair per warp

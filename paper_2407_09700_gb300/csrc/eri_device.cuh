@@ -372,14 +372,111 @@ template <> struct PairOf<double> { typedef PrimPair type; };
 template <> struct PairOf<float> { typedef PrimPairF type; };
 
 
+// Digestion of one contracted quartet (ab|cd) from shared memory (team kernels): the team
+// copies G = (ab|cd) (rows ldg = ncd | 1 apart) and the six density blocks D_ab, D_cd, D_ac,
+// D_bd, D_ad, D_bc of each density into its shared region, then every output element of
+// J~ and K~ is a dot product over shared data followed by one atomic.  The sums run in the
+// same order as in the global-memory form below, so both give the same bits.  Every lane
+// of the warp calls it (warp synchronisations inside).
+template <int TS>
+__device__ __forceinline__ void digest_shared(const TaskCtx& tc, const ClassDesc& c, const double* G, int sab, int scd,
+                                              double* sh, int tl, bool active, double w, int p0, int q0b, int r0,
+                                              int s0) {
+  const int na = c.na, nb = c.nb, nc = c.nc, nd = c.nd, nab = na * nb, ncd = nc * nd;
+  const int ldg = ncd | 1;
+  double* Gs = sh;
+  double* Dab = Gs + nab * ldg;
+  double* Dcd = Dab + nab;
+  double* Dac = Dcd + ncd;
+  double* Dbd = Dac + na * nc;
+  double* Dad = Dbd + nb * nd;
+  double* Dbc = Dad + na * nd;
+  const int nbf = tc.nbf;
+  if (active)
+    for (int t = tl; t < nab * ncd; t += TS) {
+      const int ab = t / ncd, cd = t - (t / ncd) * ncd;
+      Gs[ab * ldg + cd] = G[ab * sab + cd * scd];
+    }
+  const int nDw = warp_max(active ? tc.nD : 0);
+  for (int xd = 0; xd < nDw; ++xd) {
+    const bool on = active && xd < tc.nD;
+    const double* Dx = tc.D + (size_t)xd * nbf * nbf;
+    if (on) {
+      for (int t = tl; t < nab; t += TS) Dab[t] = __ldg(Dx + (size_t)(p0 + t / nb) * nbf + q0b + t % nb);
+      for (int t = tl; t < ncd; t += TS) Dcd[t] = __ldg(Dx + (size_t)(r0 + t / nd) * nbf + s0 + t % nd);
+      for (int t = tl; t < na * nc; t += TS) Dac[t] = __ldg(Dx + (size_t)(p0 + t / nc) * nbf + r0 + t % nc);
+      for (int t = tl; t < nb * nd; t += TS) Dbd[t] = __ldg(Dx + (size_t)(q0b + t / nd) * nbf + s0 + t % nd);
+      for (int t = tl; t < na * nd; t += TS) Dad[t] = __ldg(Dx + (size_t)(p0 + t / nd) * nbf + s0 + t % nd);
+      for (int t = tl; t < nb * nc; t += TS) Dbc[t] = __ldg(Dx + (size_t)(q0b + t / nc) * nbf + r0 + t % nc);
+    }
+    __syncwarp();
+    if (on) {
+      if (tc.want & 1) {
+        double* Jx = tc.J + (size_t)xd * nbf * nbf;
+        for (int t = tl; t < nab; t += TS) {
+          double s = 0.0;
+#pragma unroll 4
+          for (int cd = 0; cd < ncd; ++cd) s = fma(Gs[t * ldg + cd], Dcd[cd], s);
+          atomicAdd(Jx + (size_t)(p0 + t / nb) * nbf + q0b + t % nb, 2.0 * w * s);
+        }
+        for (int t = tl; t < ncd; t += TS) {
+          double s = 0.0;
+#pragma unroll 4
+          for (int ab = 0; ab < nab; ++ab) s = fma(Gs[ab * ldg + t], Dab[ab], s);
+          atomicAdd(Jx + (size_t)(r0 + t / nd) * nbf + s0 + t % nd, 2.0 * w * s);
+        }
+      }
+      if (tc.want & 2) {
+        double* Kx = tc.K + (size_t)xd * nbf * nbf;
+        for (int t = tl; t < na * nc; t += TS) {          // K_ac += w sum_bd g D_bd
+          const int ia = t / nc, ic = t - (t / nc) * nc;
+          double s = 0.0;
+          for (int ibb = 0; ibb < nb; ++ibb)
+            for (int id = 0; id < nd; ++id) s = fma(Gs[(ia * nb + ibb) * ldg + ic * nd + id], Dbd[ibb * nd + id], s);
+          atomicAdd(Kx + (size_t)(p0 + ia) * nbf + r0 + ic, w * s);
+        }
+        for (int t = tl; t < nb * nd; t += TS) {          // K_bd += w sum_ac g D_ac
+          const int ibb = t / nd, id = t - (t / nd) * nd;
+          double s = 0.0;
+          for (int ia = 0; ia < na; ++ia)
+            for (int ic = 0; ic < nc; ++ic) s = fma(Gs[(ia * nb + ibb) * ldg + ic * nd + id], Dac[ia * nc + ic], s);
+          atomicAdd(Kx + (size_t)(q0b + ibb) * nbf + s0 + id, w * s);
+        }
+        for (int t = tl; t < na * nd; t += TS) {          // K_ad += w sum_bc g D_bc
+          const int ia = t / nd, id = t - (t / nd) * nd;
+          double s = 0.0;
+          for (int ibb = 0; ibb < nb; ++ibb)
+            for (int ic = 0; ic < nc; ++ic) s = fma(Gs[(ia * nb + ibb) * ldg + ic * nd + id], Dbc[ibb * nc + ic], s);
+          atomicAdd(Kx + (size_t)(p0 + ia) * nbf + s0 + id, w * s);
+        }
+        for (int t = tl; t < nb * nc; t += TS) {          // K_bc += w sum_ad g D_ad
+          const int ibb = t / nc, ic = t - (t / nc) * nc;
+          double s = 0.0;
+          for (int ia = 0; ia < na; ++ia)
+            for (int id = 0; id < nd; ++id) s = fma(Gs[(ia * nb + ibb) * ldg + ic * nd + id], Dad[ia * nd + id], s);
+          atomicAdd(Kx + (size_t)(q0b + ibb) * nbf + r0 + ic, w * s);
+        }
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// Shared-memory doubles digest_shared needs for a class (G with odd rows + six D blocks).
+__host__ __device__ inline int digest_shared_doubles(int na, int nb, int nc, int nd) {
+  return na * nb * ((nc * nd) | 1) + na * nb + nc * nd + na * nc + nb * nd + na * nd + nb * nc;
+}
+
 // Transfer relations on the contracted [e0|f0] in E0, then digestion into J~ / K~ (KMODE_JK),
 // the block (KMODE_BLOCK) or the diagonal maximum (KMODE_SCHWARZ).  Team-cooperative;
-// every lane of the warp calls it.
+// every lane of the warp calls it.  Team kernels pass their shared region sh of sh_cap
+// doubles (free once the quartet's assembly is done): digestion then runs from shared
+// memory when G and the density blocks fit (digest_shared).
 template <int TS, typename R>
 __device__ __forceinline__ void finish_quartet(const KernelArgs& a, const TaskCtx& tc, const ClassDesc& c, R* E0,
                                                R* bufA, R* bufB, int tl, bool active, const double* AB,
                                                const double* CD, const ShellPair* bra, const ShellPair* ket, int ib,
-                                               int ik, long long task) {
+                                               int ik, long long task, double* sh = nullptr, int sh_cap = 0) {
   if (a.mode == KMODE_SCHWARZ) {  // [e0|e0] of the diagonal quartet (ne = nf), before the transfer
     double m = 0.0;
     if (active)
@@ -398,7 +495,17 @@ __device__ __forceinline__ void finish_quartet(const KernelArgs& a, const TaskCt
   const int scd = (c.ld > 0) ? nab : 1;
 
   // ---- 3. digestion (FP64) / output
-  if (a.mode == KMODE_JK) {
+  if (TS > 1 && sizeof(R) == 8 && a.mode == KMODE_JK && sh != nullptr &&
+      digest_shared_doubles(c.na, c.nb, c.nc, c.nd) <= sh_cap) {
+    double w = 1.0;
+    if (active) {
+      if (bra->sh0 == bra->sh1) w *= 0.5;
+      if (ket->sh0 == ket->sh1) w *= 0.5;
+      if (ib == ik) w *= 0.5;
+    }
+    digest_shared<TS>(tc, c, reinterpret_cast<const double*>(G), sab, scd, sh, tl, active, w,
+                      active ? bra->bf0 : 0, active ? bra->bf1 : 0, active ? ket->bf0 : 0, active ? ket->bf1 : 0);
+  } else if (a.mode == KMODE_JK) {
     if (active) {
       double w = 1.0;
       if (bra->sh0 == bra->sh1) w *= 0.5;
