@@ -415,18 +415,26 @@ def _check_blocks(m, pairs, Jl, Kl, J, K, tol):
     assert worst <= tol, worst
 
 
-@pytest.mark.parametrize("name,precision,tol", [("medium", pkg.ERI_FP64, 1e-10), ("medium", pkg.ERI_MIXED, 1e-6),
-                                                ("high_l", pkg.ERI_FP64, 1e-10), ("high_l", pkg.ERI_MIXED, 1e-6)])
-def test_jk_full_size_sampled_blocks(name, precision, tol):
+@pytest.mark.parametrize("name,precision,tol,min_tasks", [("medium", pkg.ERI_FP64, 1e-10, None),
+                                                          ("medium", pkg.ERI_MIXED, 1e-6, None),
+                                                          ("high_l", pkg.ERI_FP64, 1e-10, None),
+                                                          ("high_l", pkg.ERI_MIXED, 1e-6, None),
+                                                          ("high_l", pkg.ERI_MIXED, 1e-6, 0)])
+def test_jk_full_size_sampled_blocks(name, precision, tol, min_tasks):
     """The 30-atom medium build the benchmark times (and the 12-atom s..g build) through
     eri_jk in its launch configuration, against oracle J / K blocks on sampled shell pairs
-    covering every pair of angular momenta; the mixed builds at the split 1e-4."""
+    covering every pair of angular momenta; the mixed builds at the split 1e-4.  The s..g
+    build's classes are below the default minimum size of an FP32 launch, so it also runs
+    with no minimum: every class up to (gg|gg) then has FP32 quartets."""
     m, pairs, Jl, Kl = _full_case(name)
-    plan = pkg.Plan(m, precision=precision, mixed_thresh=MIXED_THRESH)
+    kw = {} if min_tasks is None else {"mixed_min_tasks": min_tasks}
+    plan = pkg.Plan(m, precision=precision, mixed_thresh=MIXED_THRESH, **kw)
     J, K = _jk_gpu(plan, m.D)
     _check_blocks(m, pairs, Jl, Kl, J, K, tol)
     st = plan.stats()
     assert st["quartets_computed"] > 0
+    if min_tasks == 0:
+        assert st["quartets_fp32"] > 0
 
 
 def test_check_symmetric_option_rejects_asymmetric_density():
