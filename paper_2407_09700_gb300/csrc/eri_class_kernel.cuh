@@ -32,9 +32,13 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : ((sizeof(R) == 4 && !XY) ?
   static_assert(!STAGE || (TS > 1 && sizeof(R) == 8), "staging is for FP64 team kernels");
   extern __shared__ double smem[];
   typedef typename PairOf<R>::type PP;
-  constexpr int TEAMS_PER_WARP = 32 / TS;
+  // TS = TPB: one team per block (its warps share the quartet, the batch tables and the
+  // scratch; team barriers are __syncthreads)
+  constexpr bool BLK = TS > 32;
+  static_assert(!BLK || TS == TPB, "a team is a warp's part or the whole block");
+  constexpr int TEAMS_PER_WARP = BLK ? 1 : 32 / TS;
   const int lane = threadIdx.x & 31;
-  const int tl = lane % TS;                          // lane within team
+  const int tl = BLK ? (int)threadIdx.x : lane % TS;  // lane within team
   const int team_in_block = threadIdx.x / TS;
   const long long gteam = (long long)blockIdx.x * (TPB / TS) + team_in_block;
   const ClassDesc& c = a.c;
@@ -93,12 +97,20 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : ((sizeof(R) == 4 && !XY) ?
   const long long ntask = listed ? (long long)*a.tcount : a.ntask;
 
   while (true) {
-    // ---- fetch TEAMS_PER_WARP tasks per warp
+    // ---- fetch TEAMS_PER_WARP tasks per warp (one per block for a block-wide team)
     unsigned long long tbase = 0;
-    if (lane == 0) tbase = atomicAdd(a.counter, (unsigned long long)TEAMS_PER_WARP);
-    tbase = __shfl_sync(0xffffffffu, tbase, 0);
+    if constexpr (BLK) {
+      __shared__ unsigned long long s_tbase;
+      if (threadIdx.x == 0) s_tbase = atomicAdd(a.counter, 1ull);
+      __syncthreads();
+      tbase = s_tbase;
+      __syncthreads();
+    } else {
+      if (lane == 0) tbase = atomicAdd(a.counter, (unsigned long long)TEAMS_PER_WARP);
+      tbase = __shfl_sync(0xffffffffu, tbase, 0);
+    }
     if (tbase >= (unsigned long long)ntask) break;
-    const long long task = (long long)tbase + lane / TS;
+    const long long task = (long long)tbase + (BLK ? 0 : lane / TS);
     bool active = task < ntask;
 
     // ---- decode the task into (bra pair, ket pair)
@@ -261,7 +273,7 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : ((sizeof(R) == 4 && !XY) ?
           sr[o + 17] = he;
         }
       }
-      __syncwarp();
+      team_sync<TS>();
       // ---- b. roots, weights (FP64) and 2D integrals (R) per (primitive, root), or per
       //      (primitive, root, axis) when that fills more of the team's lanes
       if (TS > 1 && (XY ? c.split3_xy : c.split3)) {
@@ -306,7 +318,7 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : ((sizeof(R) == 4 && !XY) ?
           }
         }
       }
-      __syncwarp();
+      team_sync<TS>();
     };
     // ---- c. of one batch for the current pass
     auto assemble = [&](int nbt) {
@@ -334,7 +346,7 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : ((sizeof(R) == 4 && !XY) ?
           }
         };
         if (nsteps > 0) form(0);
-        __syncwarp();
+        team_sync<TS>();
         for (int st = 0; st < nsteps; ++st) {
           if (st + 1 < nsteps) form(st + 1);
           const int jj = st / N, nn = st - (st / N) * N;
@@ -349,7 +361,7 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : ((sizeof(R) == 4 && !XY) ?
               acc[k] = jv ? v : acc[k];
             }
           }
-          __syncwarp();
+          team_sync<TS>();
         }
       } else {
         // lane programs: a slot that starts a group forms the group's I_x I_y product, the
@@ -373,7 +385,7 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : ((sizeof(R) == 4 && !XY) ?
           }
         }
       }
-      __syncwarp();
+      team_sync<TS>();
     };
     const int nbatch = (maxq + bp - 1) / bp;        // uniform
     if (sizeof(R) == 8 && npass > 1) {
@@ -397,13 +409,13 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : ((sizeof(R) == 4 && !XY) ?
         end_pass(true);
       }
     }
-    __syncwarp();
+    team_sync<TS>();
 
     // the team's shared region is free here: team kernels digest from it
     finish_quartet<TS, double>(a, tc, c, E0, bufA, bufB, tl, active, AB, CD, bra, ket, ib, ik, task,
                                TS > 1 ? sd.base : nullptr,
                                XY ? c.team_doubles_xy : (sizeof(R) == 8 ? c.team_doubles : c.team_doubles_f32));
-    __syncwarp();
+    team_sync<TS>();
   }
   // ---- counters: one atomic pair per warp
   for (int off = 16; off > 0; off >>= 1) {

@@ -185,8 +185,9 @@ __device__ __forceinline__ void rys_2d1(const Smem<R>& g, int o, int Le, int Lf,
 // ------------------------------------------------------------------ transfer (horizontal) relations
 // Input element (e, v) at X[e*xe + v*xv] for la <= |e| <= la+lb (e relative to cart_below(la)).
 // Output contiguous [a][b][v] with |a| = la, |b| = lb; returns the output pointer (X when lb = 0).
-// Team-cooperative; every lane of the warp must call it (it contains __syncwarp).
-template <typename R>
+// Team-cooperative; every thread of the team must call it (it contains team barriers:
+// __syncwarp, or __syncthreads for a block-wide team, BLK).
+template <typename R, bool BLK = false>
 __device__ const R* hrr_team(int la, int lb, const double* AB, int nv, const R* X, int xe, int xv, R* bufA,
                              R* bufB, int tl, int TS, bool active) {
   const R ABr[3] = {(R)AB[0], (R)AB[1], (R)AB[2]};
@@ -197,9 +198,27 @@ __device__ const R* hrr_team(int la, int lb, const double* AB, int nv, const R* 
     R* nxt = (cur == bufA) ? bufB : bufA;
     const int na = cart_below(la + lb - k + 1) - base;
     const int nb = (k + 1) * (k + 2) / 2;
-    const int total = na * nb * nv;
-    if (active) {
-      for (int t = tl; t < total; t += TS) {
+    // output row r = (ia, ib) of the level: its two input rows (a + 1_i, b - 1_i) and
+    // (a, b - 1_i) and the axis i that b was built along
+    auto row = [&](int r, const R*& hi, const R*& lo, R& f) {
+      const int ia = r / nb, ib = r - (r / nb) * nb;
+      const uchar4 av = cart_of(base + ia);
+      const uchar4 bv = cart_of(cart_below(k) + ib);
+      const int i = bv.x ? 0 : (bv.y ? 1 : 2);
+      int bm[3] = {bv.x, bv.y, bv.z};
+      bm[i] -= 1;
+      const int ibm = cart_pos(bm[1], bm[2]);
+      int ap[3] = {av.x, av.y, av.z};
+      ap[i] += 1;
+      const int iap = cart_index(ap[0], ap[1], ap[2]) - base;
+      hi = cur + iap * cse + ibm * csb;
+      lo = cur + ia * cse + ibm * csb;
+      f = (i == 0) ? ABr[0] : (i == 1 ? ABr[1] : ABr[2]);
+    };
+    if (active && !BLK) {
+      // warp teams: one output per lane at a time (measured faster for them, and for the
+      // gradient's many small blocks, than the forms below)
+      for (int t = tl; t < na * nb * nv; t += TS) {
         const int v = t % nv;
         const int r = t / nv;
         const int ib = r % nb;
@@ -217,8 +236,65 @@ __device__ const R* hrr_team(int la, int lb, const double* AB, int nv, const R* 
         const R lo = cur[ia * cse + ibm * csb + v * csv];
         nxt[(ia * nb + ib) * nv + v] = fma(ABr[i], lo, hi);
       }
+    } else if (active) {
+      const int nr = na * nb;
+      if (nv >= TS) {
+        // block teams, long rows: rows in groups of four, the team's lanes along v; the
+        // index arithmetic runs once per row, consecutive lanes touch consecutive outputs,
+        // and the eight loads of a group are in flight together (the transfer phase of a
+        // block team reads L2 / DRAM-resident scratch: 12-atom s..g build 1067 -> 1035 ms)
+        int r = 0;
+        for (; r + 4 <= nr; r += 4) {
+          const R *h0, *l0, *h1, *l1, *h2, *l2, *h3, *l3;
+          R f0, f1, f2, f3;
+          row(r, h0, l0, f0);
+          row(r + 1, h1, l1, f1);
+          row(r + 2, h2, l2, f2);
+          row(r + 3, h3, l3, f3);
+          R* o = nxt + r * nv;
+          for (int v = tl; v < nv; v += TS) {
+            const int vo = v * csv;
+            const R a0 = h0[vo], b0 = l0[vo], a1 = h1[vo], b1 = l1[vo];
+            const R a2 = h2[vo], b2 = l2[vo], a3 = h3[vo], b3 = l3[vo];
+            o[v] = fma(f0, b0, a0);
+            o[nv + v] = fma(f1, b1, a1);
+            o[2 * nv + v] = fma(f2, b2, a2);
+            o[3 * nv + v] = fma(f3, b3, a3);
+          }
+        }
+        for (; r < nr; ++r) {
+          const R *h0, *l0;
+          R f0;
+          row(r, h0, l0, f0);
+          R* o = nxt + r * nv;
+          for (int v = tl; v < nv; v += TS) o[v] = fma(f0, l0[v * csv], h0[v * csv]);
+        }
+      } else {
+        // short rows: the outputs in order over all lanes, four per lane at a time (the
+        // loads of the four before their stores)
+        const int nt = nr * nv;
+        for (int t0 = tl; t0 < nt; t0 += 4 * TS) {
+          R hv[4], lv[4], fv[4];
+          int dst[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int t = t0 + u * TS;
+            dst[u] = t < nt ? t : -1;
+            const int tt = t < nt ? t : 0;
+            const int r = tt / nv, v = tt - (tt / nv) * nv;
+            const R *h0, *l0;
+            row(r, h0, l0, fv[u]);
+            hv[u] = h0[v * csv];
+            lv[u] = l0[v * csv];
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (dst[u] >= 0) nxt[dst[u]] = fma(fv[u], lv[u], hv[u]);
+        }
+      }
     }
-    __syncwarp();
+    if (BLK) __syncthreads();
+    else __syncwarp();
     cur = nxt;
     cse = nb * nv;
     csb = nv;
@@ -270,6 +346,31 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsig
 
 // ------------------------------------------------------------------ warp helpers
 __device__ __forceinline__ int warp_max(int v) { return __reduce_max_sync(0xffffffffu, v); }
+
+// Team of TS lanes: TS <= 32 lanes share a warp (32 / TS teams per warp); TS = TPB is the
+// whole block (one team per block, several warps).  team_sync orders the team's shared and
+// scratch accesses; every thread of the team must call it.
+template <int TS>
+__device__ __forceinline__ void team_sync() {
+  if (TS > 32) __syncthreads();
+  else __syncwarp();
+}
+// Maximum of m over the TS lanes of a team (every thread of the team calls it).
+template <int TS>
+__device__ __forceinline__ double team_max(double m) {
+  if (TS <= 1) return m;
+  constexpr int W = TS < 32 ? TS : 32;
+  for (int off = W / 2; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
+  if constexpr (TS > 32) {
+    __shared__ double wmax[TS / 32];
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+    __syncthreads();
+    m = wmax[0];
+    for (int w = 1; w < TS / 32; ++w) m = fmax(m, wmax[w]);
+  }
+  return m;
+}
 
 // ------------------------------------------------------------------ task decoding and screening
 // Task t of a class enumerates (bra pair, ket pair): rectangular bra x ket, or the
@@ -377,7 +478,7 @@ template <> struct PairOf<float> { typedef PrimPairF type; };
 // D_bd, D_ad, D_bc of each density into its shared region, then every output element of
 // J~ and K~ is a dot product over shared data followed by one atomic.  The sums run in the
 // same order as in the global-memory form below, so both give the same bits.  Every lane
-// of the warp calls it (warp synchronisations inside).
+// of the team calls it (team synchronisations inside).
 template <int TS>
 __device__ __forceinline__ void digest_shared(const TaskCtx& tc, const ClassDesc& c, const double* G, int sab, int scd,
                                               double* sh, int tl, bool active, double w, int p0, int q0b, int r0,
@@ -409,7 +510,7 @@ __device__ __forceinline__ void digest_shared(const TaskCtx& tc, const ClassDesc
       for (int t = tl; t < na * nd; t += TS) Dad[t] = __ldg(Dx + (size_t)(p0 + t / nd) * nbf + s0 + t % nd);
       for (int t = tl; t < nb * nc; t += TS) Dbc[t] = __ldg(Dx + (size_t)(q0b + t / nc) * nbf + r0 + t % nc);
     }
-    __syncwarp();
+    team_sync<TS>();
     if (on) {
       if (tc.want & 1) {
         double* Jx = tc.J + (size_t)xd * nbf * nbf;
@@ -458,7 +559,7 @@ __device__ __forceinline__ void digest_shared(const TaskCtx& tc, const ClassDesc
         }
       }
     }
-    __syncwarp();
+    team_sync<TS>();
   }
 }
 
@@ -469,7 +570,7 @@ __host__ __device__ inline int digest_shared_doubles(int na, int nb, int nc, int
 
 // Transfer relations on the contracted [e0|f0] in E0, then digestion into J~ / K~ (KMODE_JK),
 // the block (KMODE_BLOCK) or the diagonal maximum (KMODE_SCHWARZ).  Team-cooperative;
-// every lane of the warp calls it.  Team kernels pass their shared region sh of sh_cap
+// every thread of the team calls it.  Team kernels pass their shared region sh of sh_cap
 // doubles (free once the quartet's assembly is done): digestion then runs from shared
 // memory when G and the density blocks fit (digest_shared).
 template <int TS, typename R>
@@ -481,15 +582,13 @@ __device__ __forceinline__ void finish_quartet(const KernelArgs& a, const TaskCt
     double m = 0.0;
     if (active)
       for (int e = tl; e < c.ne; e += TS) m = fmax(m, fabs((double)E0[e * c.nf + e]));
-    if (TS > 1) {
-      for (int off = TS / 2; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
-    }
+    m = team_max<TS>(m);
     if (active && tl == 0) a.qout[a.ntask + task] = m;
   }
   // ---- 2. transfer relations: bra on e (vector over f), then ket on f (vector over ab)
   const int nab = c.na * c.nb, ncd = c.nc * c.nd;
-  const R* Y = hrr_team<R>(c.la, c.lb, AB, c.nf, E0, c.nf, 1, bufA, bufB, tl, TS, active);
-  const R* G = hrr_team<R>(c.lc, c.ld, CD, nab, Y, 1, c.nf, bufA, bufB, tl, TS, active);
+  const R* Y = hrr_team<R, (TS > 32)>(c.la, c.lb, AB, c.nf, E0, c.nf, 1, bufA, bufB, tl, TS, active);
+  const R* G = hrr_team<R, (TS > 32)>(c.lc, c.ld, CD, nab, Y, 1, c.nf, bufA, bufB, tl, TS, active);
   // (ab|cd) = G[ab*sab + cd*scd]
   const int sab = (c.ld > 0) ? 1 : c.nf;
   const int scd = (c.ld > 0) ? nab : 1;
@@ -594,9 +693,7 @@ __device__ __forceinline__ void finish_quartet(const KernelArgs& a, const TaskCt
     double m = 0.0;
     if (active)
       for (int t = tl; t < nab; t += TS) m = fmax(m, fabs((double)G[t * sab + t * scd]));
-    if (TS > 1) {
-      for (int off = TS / 2; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
-    }
+    m = team_max<TS>(m);
     if (active && tl == 0) a.qout[task] = m;
   }
 }

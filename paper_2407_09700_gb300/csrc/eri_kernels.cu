@@ -264,6 +264,7 @@ static const void* class_kernel_ptr(int ts, int fp32, int xy) {
       case 8: return (const void*)eri_class_kernel<4, float, false>;
       case 16: return (const void*)eri_class_kernel<8, float, false>;
       case 64: return (const void*)eri_class_kernel<32, float, false>;
+      case 256: return (const void*)eri_class_kernel<128, float, false>;
     }
   } else {
     switch (ts * 2 + (xy ? 1 : 0)) {
@@ -276,6 +277,8 @@ static const void* class_kernel_ptr(int ts, int fp32, int xy) {
       case 17: return (const void*)eri_class_kernel<8, double, true>;
       case 64: return (const void*)eri_class_kernel<32, double, false>;
       case 65: return (const void*)eri_class_kernel<32, double, true>;
+      case 256: return (const void*)eri_class_kernel<128, double, false>;
+      case 257: return (const void*)eri_class_kernel<128, double, true>;
     }
   }
   return nullptr;
@@ -310,6 +313,7 @@ extern "C" int erik_launch_class(int ts, int fp32, const KernelArgs* a, int grid
       case 4: CLASS_LAUNCH(4, float) break;
       case 8: CLASS_LAUNCH(8, float) break;
       case 32: CLASS_LAUNCH(32, float) break;
+      case 128: CLASS_LAUNCH(128, float) break;
       default: return (int)cudaErrorInvalidValue;
     }
   } else {
@@ -319,6 +323,7 @@ extern "C" int erik_launch_class(int ts, int fp32, const KernelArgs* a, int grid
       case 4: CLASS_LAUNCH(4, double) break;
       case 8: CLASS_LAUNCH(8, double) break;
       case 32: CLASS_LAUNCH(32, double) break;
+      case 128: CLASS_LAUNCH(128, double) break;
       default: return (int)cudaErrorInvalidValue;
     }
   }

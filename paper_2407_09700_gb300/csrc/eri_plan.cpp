@@ -103,9 +103,39 @@ int choose_ts(int nout) {
   return 32;
 }
 
+// Block-wide teams (128 lanes, the whole block on one quartet) for the classes with at
+// least block_team_min_out() contracted [e0|f0] values: at 32 lanes such a class needs
+// several output passes, a batch holds one or two primitive quartets, and every batch
+// reloads and restores all partial sums from the team's scratch, while 8 teams per SM hold
+// ~1 GB of scratch (far beyond L2).  One team per block with the block's shared memory
+// (two blocks per SM) holds ~6 primitive quartets per batch and a quarter of the scratch.
+// Measured on the 12-atom s..g build: 1248 ms with 32-lane teams, 1067 ms with block teams
+// (lane programs) at two blocks per SM, 1918 ms at one block per SM (four warps do not keep
+// the FP64 pipe busy through the team barriers and the transfer phase); block teams from
+// 1024 values: 1088 ms.
+// ERI_BLOCK_TEAM="min_values budget_doubles" overrides both (tuning on new hardware).
+struct BlockTeam { int min_out = 2048, budget = 12000; };
+const BlockTeam& block_team() {
+  static BlockTeam bt;
+  static bool read = false;
+  if (!read) {
+    read = true;
+    if (const char* env = std::getenv("ERI_BLOCK_TEAM")) {
+      int m = 0, b = 0;
+      if (sscanf(env, "%d %d", &m, &b) == 2 && m > 0 && b >= 1024 && b <= 25000) {
+        bt.min_out = m;
+        bt.budget = b;
+      }
+    }
+  }
+  return bt;
+}
+
 // Shared-memory doubles per team for the batch tables: about 98 KB per 128-thread block,
-// so two blocks fit on an SM.
-int team_budget(int ts) { return ts == 2 ? 192 : ts == 4 ? 384 : ts == 8 ? 768 : 3072; }
+// so two blocks fit on an SM (block-wide teams: the block_team() budget).
+int team_budget(int ts) {
+  return ts == 2 ? 192 : ts == 4 ? 384 : ts == 8 ? 768 : ts == 128 ? block_team().budget : 3072;
+}
 
 // Shared-memory stride between the team regions of a block.  With TS lanes per team, the
 // 32 / TS teams of a warp read the same table entries at the same time; a stride of TS
@@ -158,7 +188,7 @@ ClassTune class_tune(int la, int lb, int lc, int ld) {
     }
   for (const auto& v : table)
     if (v[0] == la && v[1] == lb && v[2] == lc && v[3] == ld) {
-      if (v[4] == 1 || v[4] == 2 || v[4] == 4 || v[4] == 8 || v[4] == 32) t.ts = v[4];
+      if (v[4] == 1 || v[4] == 2 || v[4] == 4 || v[4] == 8 || v[4] == 32 || v[4] == 128) t.ts = v[4];
       t.xy = v[5];
       t.stage = v[6] == 1 ? 1 : 0;
     }
@@ -263,7 +293,7 @@ void make_class(int la, int lb, int lc, int ld, ClassDesc* c, int* ts, std::vect
   idx->clear();
   const int L1 = c->Lf + 1;
   const ClassTune tune = class_tune(la, lb, lc, ld);
-  *ts = tune.ts > 0 ? tune.ts : choose_ts(c->nout);
+  *ts = tune.ts > 0 ? tune.ts : (c->nout >= block_team().min_out ? 128 : choose_ts(c->nout));
   c->stage = (tune.stage && *ts == 8 && la == 2 && lb == 1 && lc == 2 && ld == 1) ? 1 : 0;
   const int T = *ts;
   const int per_pass = T * 32;
@@ -361,7 +391,10 @@ void make_class(int la, int lb, int lc, int ld, ClassDesc* c, int* ts, std::vect
     const int bp_on = std::max(1, std::min(32, (team_budget(T) - 2 * xymax) / per_prim));
     auto iters = [&](int bp) { return (double)((bp * c->nroots + T - 1) / T) / bp; };
     const bool fills = iters(bp_on) <= 1.1 * iters(c->bp);
-    c->xy = (kcnt >= 20 && 5 * xysum <= 4 * c->nout && fills) ? 1 : 0;
+    // block-wide teams run lane programs: the shared products' barrier per (primitive, root)
+    // step stalls four warps at once (12-atom s..g build: 1067 ms with lane programs for
+    // every block-team class, 1153 ms with the rule below, 1255 ms with shared products)
+    c->xy = (T <= 32 && kcnt >= 20 && 5 * xysum <= 4 * c->nout && fills) ? 1 : 0;
     if (tune.xy >= 0) c->xy = tune.xy ? 1 : 0;
     if (c->xy) {
       c->xy_npass = xnp;
