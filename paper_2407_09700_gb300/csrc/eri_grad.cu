@@ -92,10 +92,10 @@ __device__ __forceinline__ const double* shifted_block(const double* S, int snf,
                                                        int& scd) {
   const int nv = cart_below(lc_ + ld_ + 1) - cart_below(lc_);
   const double* X = S + (size_t)eo * snf + fo;
-  const double* Y = hrr_team<double>(la_, lb_, AB, nv, X, snf, 1, bufA, bufB, tl, TS, active);
+  const double* Y = hrr_team<double, (TS > 32)>(la_, lb_, AB, nv, X, snf, 1, bufA, bufB, tl, TS, active);
   const int sab1 = (lb_ > 0) ? nv : snf;
   const int nab = ncart_d(la_) * ncart_d(lb_);
-  const double* G = hrr_team<double>(lc_, ld_, CD, nab, Y, 1, sab1, bufA, bufB, tl, TS, active);
+  const double* G = hrr_team<double, (TS > 32)>(lc_, ld_, CD, nab, Y, 1, sab1, bufA, bufB, tl, TS, active);
   if (ld_ > 0) {
     sab = 1;
     scd = nab;
@@ -111,9 +111,12 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : 2)) eri_grad_kernel(const 
   extern __shared__ double smem[];
   const KernelArgs& a = ga.k;
   const GradDesc& g = ga.g;
-  constexpr int TEAMS_PER_WARP = 32 / TS;
+  // TS = TPB: one team per block (team barriers are __syncthreads), as in the J/K kernel
+  constexpr bool BLK = TS > 32;
+  static_assert(!BLK || TS == TPB, "a team is a warp's part or the whole block");
+  constexpr int TEAMS_PER_WARP = BLK ? 1 : 32 / TS;
   const int lane = threadIdx.x & 31;
-  const int tl = lane % TS;
+  const int tl = BLK ? (int)threadIdx.x : lane % TS;
   const int team_in_block = threadIdx.x / TS;
   const long long gteam = (long long)blockIdx.x * (TPB / TS) + team_in_block;
   const int N = g.nroots, nI = g.nI, Le2 = g.Le2, Lf2 = g.Lf2;
@@ -148,10 +151,18 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : 2)) eri_grad_kernel(const 
 
   while (true) {
     unsigned long long tbase = 0;
-    if (lane == 0) tbase = atomicAdd(a.counter, (unsigned long long)TEAMS_PER_WARP);
-    tbase = __shfl_sync(0xffffffffu, tbase, 0);
+    if constexpr (BLK) {
+      __shared__ unsigned long long s_tbase;
+      if (threadIdx.x == 0) s_tbase = atomicAdd(a.counter, 1ull);
+      __syncthreads();
+      tbase = s_tbase;
+      __syncthreads();
+    } else {
+      if (lane == 0) tbase = atomicAdd(a.counter, (unsigned long long)TEAMS_PER_WARP);
+      tbase = __shfl_sync(0xffffffffu, tbase, 0);
+    }
     if (tbase >= (unsigned long long)ntask) break;
-    const long long task = (long long)tbase + lane / TS;
+    const long long task = (long long)tbase + (BLK ? 0 : lane / TS);
     const bool active = task < ntask;
 
     int ib = 0, ik = 0;
@@ -257,7 +268,7 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : 2)) eri_grad_kernel(const 
           sr[o + 20] = 2.0 * y->alpha;
         }
       }
-      __syncwarp();
+      team_sync<TS>();
       // b. roots, weights and the 2D tables per (primitive, root), or per (primitive, root,
       //    axis) when that fills more of the team's lanes
       if (TS > 1 && g.split3) {
@@ -318,7 +329,7 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : 2)) eri_grad_kernel(const 
           }
         }
       }
-      __syncwarp();
+      team_sync<TS>();
     };
     auto assemble = [&](int nbt) {
       // c. assembly and contraction in registers by lane programs: a slot that starts a
@@ -341,7 +352,7 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : 2)) eri_grad_kernel(const 
           }
         }
       }
-      __syncwarp();
+      team_sync<TS>();
     };
     const int nbatch = (maxq + bp - 1) / bp;        // uniform
     if (g.npass > 1) {
@@ -363,7 +374,7 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : 2)) eri_grad_kernel(const 
       }
       end_pass(true);
     }
-    __syncwarp();
+    team_sync<TS>();
 
     // ---- Gamma_J, Gamma_K of this quartet
     if (active) {
@@ -390,7 +401,7 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : 2)) eri_grad_kernel(const 
         GK[t] = -w * fma(dac, dbd, dad * dbc);
       }
     }
-    __syncwarp();
+    team_sync<TS>();
 
     // ---- 2-3. the six shifted blocks, contracted with Gamma
     double jA[3] = {0, 0, 0}, jB[3] = {0, 0, 0}, jC[3] = {0, 0, 0};
@@ -405,39 +416,40 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : 2)) eri_grad_kernel(const 
     G = shifted_block<TS>(scr + g.s_off[1], g.s_nf[1], 0, 0, la + 1, lb, lc, ld, AB, CD, bufA, bufB, tl, active,
                           sab, scd);
     contract_shift<TS>(G, sab, scd, 0, la + 1, true, nbase, GJ, GK, tl, active, jA, kA);
-    __syncwarp();
+    team_sync<TS>();
     if (la > 0) {  // A- : (a-1 b|cd) from the unweighted set
       G = shifted_block<TS>(S0, g.s_nf[0], 0, f0col, la - 1, lb, lc, ld, AB, CD, bufA, bufB, tl, active, sab, scd);
       contract_shift<TS>(G, sab, scd, 0, la - 1, false, nbase, GJ, GK, tl, active, jA, kA);
-      __syncwarp();
+      team_sync<TS>();
     }
     // B+ : (a b+1|cd) from the 2 beta set
     G = shifted_block<TS>(scr + g.s_off[2], g.s_nf[2], 0, 0, la, lb + 1, lc, ld, AB, CD, bufA, bufB, tl, active,
                           sab, scd);
     contract_shift<TS>(G, sab, scd, 1, lb + 1, true, nbase, GJ, GK, tl, active, jB, kB);
-    __syncwarp();
+    team_sync<TS>();
     if (lb > 0) {  // B- : (a b-1|cd)
       G = shifted_block<TS>(S0, g.s_nf[0], e0row, f0col, la, lb - 1, lc, ld, AB, CD, bufA, bufB, tl, active, sab,
                             scd);
       contract_shift<TS>(G, sab, scd, 1, lb - 1, false, nbase, GJ, GK, tl, active, jB, kB);
-      __syncwarp();
+      team_sync<TS>();
     }
     // C+ : (ab|c+1 d) from the 2 gamma set
     G = shifted_block<TS>(scr + g.s_off[3], g.s_nf[3], 0, 0, la, lb, lc + 1, ld, AB, CD, bufA, bufB, tl, active,
                           sab, scd);
     contract_shift<TS>(G, sab, scd, 2, lc + 1, true, nbase, GJ, GK, tl, active, jC, kC);
-    __syncwarp();
+    team_sync<TS>();
     if (lc > 0) {  // C- : (ab|c-1 d)
       G = shifted_block<TS>(S0, g.s_nf[0], e0row, 0, la, lb, lc - 1, ld, AB, CD, bufA, bufB, tl, active, sab, scd);
       contract_shift<TS>(G, sab, scd, 2, lc - 1, false, nbase, GJ, GK, tl, active, jC, kC);
-      __syncwarp();
+      team_sync<TS>();
     }
 
     // ---- team reduction and the once-per-quartet atomics
     if (TS > 1) {
+      constexpr int W = TS < 32 ? TS : 32;
 #pragma unroll
       for (int x = 0; x < 3; ++x) {
-        for (int off = TS / 2; off > 0; off >>= 1) {
+        for (int off = W / 2; off > 0; off >>= 1) {
           jA[x] += __shfl_xor_sync(0xffffffffu, jA[x], off);
           jB[x] += __shfl_xor_sync(0xffffffffu, jB[x], off);
           jC[x] += __shfl_xor_sync(0xffffffffu, jC[x], off);
@@ -446,6 +458,29 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : 2)) eri_grad_kernel(const 
           kC[x] += __shfl_xor_sync(0xffffffffu, kC[x], off);
         }
       }
+    }
+    if constexpr (BLK) {       // the block's warps: partial sums through shared memory
+      __shared__ double red[TS / 32][18];
+      if (lane == 0)
+        for (int x = 0; x < 3; ++x) {
+          red[threadIdx.x >> 5][x] = jA[x];
+          red[threadIdx.x >> 5][3 + x] = jB[x];
+          red[threadIdx.x >> 5][6 + x] = jC[x];
+          red[threadIdx.x >> 5][9 + x] = kA[x];
+          red[threadIdx.x >> 5][12 + x] = kB[x];
+          red[threadIdx.x >> 5][15 + x] = kC[x];
+        }
+      __syncthreads();
+      if (threadIdx.x == 0)
+        for (int w = 1; w < TS / 32; ++w)
+          for (int x = 0; x < 3; ++x) {
+            jA[x] += red[w][x];
+            jB[x] += red[w][3 + x];
+            jC[x] += red[w][6 + x];
+            kA[x] += red[w][9 + x];
+            kB[x] += red[w][12 + x];
+            kC[x] += red[w][15 + x];
+          }
     }
     if (active && tl == 0) {
       const int atA = __ldg(ga.sh_atom + bra->sh0), atB = __ldg(ga.sh_atom + bra->sh1);
@@ -462,7 +497,7 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : 2)) eri_grad_kernel(const 
         atomicAdd(ga.gK + 3 * atD + x, -(kA[x] + kB[x] + kC[x]));
       }
     }
-    __syncwarp();
+    team_sync<TS>();
   }
   for (int off = 16; off > 0; off >>= 1) {
     cnt_q += __shfl_xor_sync(0xffffffffu, cnt_q, off);
@@ -482,6 +517,7 @@ static const void* grad_kernel_ptr(int ts) {
     case 1: return (const void*)eri_grad_kernel<1>;
     case 8: return (const void*)eri_grad_kernel<8>;
     case 32: return (const void*)eri_grad_kernel<32>;
+    case 128: return (const void*)eri_grad_kernel<128>;
   }
   return nullptr;
 }
@@ -500,6 +536,7 @@ extern "C" int erik_launch_grad(int ts, const GradArgs* a, int grid, int smem_by
     case 1: eri_grad_kernel<1><<<grid, TPB, smem_bytes, s>>>(*a); break;
     case 8: eri_grad_kernel<8><<<grid, TPB, smem_bytes, s>>>(*a); break;
     case 32: eri_grad_kernel<32><<<grid, TPB, smem_bytes, s>>>(*a); break;
+    case 128: eri_grad_kernel<128><<<grid, TPB, smem_bytes, s>>>(*a); break;
     default: return (int)cudaErrorInvalidValue;
   }
   return (int)cudaGetLastError();

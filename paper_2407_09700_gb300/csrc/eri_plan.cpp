@@ -482,7 +482,8 @@ void make_grad_class(int la, int lb, int lc, int ld, GradDesc* g, int* ts, std::
     off += g->s_ne[k] * g->s_nf[k];
   }
   g->nout = off;
-  *ts = choose_ts(g->nout);
+  // block-wide teams for the large classes, as in the J/K build
+  *ts = g->nout >= block_team().min_out ? 128 : choose_ts(g->nout);
   std::vector<int> sv;
   std::vector<uint32_t> gm;
   int Ls = 0;
