@@ -94,7 +94,8 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : ((sizeof(R) == 4 && !XY) ?
   unsigned long long cnt_q = 0, cnt_p = 0;
 
   const bool listed = (a.mode == KMODE_JK) && (a.tlist != nullptr || a.jobs != nullptr);
-  const long long ntask = listed ? (long long)*a.tcount : a.ntask;
+  const int qs = (a.mode == KMODE_JK && a.qsplit > 1) ? a.qsplit : 1;   // tasks per quartet
+  const long long ntask = (listed ? (long long)*a.tcount : a.ntask) * qs;
 
   while (true) {
     // ---- fetch TEAMS_PER_WARP tasks per warp (one per block for a block-wide team)
@@ -110,8 +111,10 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : ((sizeof(R) == 4 && !XY) ?
       tbase = __shfl_sync(0xffffffffu, tbase, 0);
     }
     if (tbase >= (unsigned long long)ntask) break;
-    const long long task = (long long)tbase + (BLK ? 0 : lane / TS);
-    bool active = task < ntask;
+    const long long slot = (long long)tbase + (BLK ? 0 : lane / TS);
+    bool active = slot < ntask;
+    const long long task = slot / qs;                // the quartet; ch: its primitive range
+    const int ch = (int)(slot - task * qs);
 
     // ---- decode the task into (bra pair, ket pair)
     int ib = 0, ik = 0;
@@ -135,9 +138,14 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : ((sizeof(R) == 4 && !XY) ?
     }
     const int npb = active ? bra->nprim : 0;
     const int npk = active ? ket->nprim : 0;
-    const int nq = npb * npk;
+    // this task's primitive quartets [qlo, qlo + nq) of the quartet's npb * npk (the last
+    // range is never empty, so it counts the quartet)
+    const int nqf = npb * npk;
+    const int qlo = (qs > 1) ? (int)((long long)ch * nqf / qs) : 0;
+    const int nq = (qs > 1) ? (int)((long long)(ch + 1) * nqf / qs) - qlo : nqf;
+    if (nq == 0) active = false;
     const int maxq = warp_max(nq);
-    if (tl == 0 && active) { cnt_q += 1; cnt_p += (unsigned long long)nq; }
+    if (tl == 0 && active) { cnt_q += (ch == qs - 1) ? 1 : 0; cnt_p += (unsigned long long)nq; }
 
     double AB[3], CD[3];
     if (active) {
@@ -235,7 +243,7 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : ((sizeof(R) == 4 && !XY) ?
       // ---- a. primitive-quartet scalars: T and the table lookup in FP64, the rest in R
       for (int j = tl; j < bp; j += TS) {
         if (j < nbt) {
-          const int q = q0 + j;
+          const int q = qlo + q0 + j;
           const int ixp = boff + q / npk, iyp = koff + q % npk;
           const PrimPair* xd = (STAGE && staged) ? stage + q / npk : tc.prims + ixp;
           const PrimPair* yd = (STAGE && staged) ? stage + npb + q % npk : tc.prims + iyp;

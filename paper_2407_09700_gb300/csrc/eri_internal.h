@@ -148,6 +148,10 @@ struct KernelArgs {
   // scheduling, scratch, counters
   unsigned long long* counter;
   double* scratch;
+  // KMODE_JK: each listed quartet runs as qsplit tasks over consecutive ranges of its
+  // primitive quartets (0 or 1: one task per quartet); the transfer relations and the
+  // digestion are linear, so every range digests its partial [e0|f0] on its own
+  int qsplit;
   unsigned long long* stats;   // [0] quartets computed, [1] primitive quartets
   unsigned* err;               // set to 1 when a bounded device wait gave up (staged kernels)
   // Rys table for this class's root count

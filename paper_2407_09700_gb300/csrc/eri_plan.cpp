@@ -690,6 +690,7 @@ struct eri_plan {
   int type_off_all[ERI_NPAIRTYPE] = {0}, type_cnt_all[ERI_NPAIRTYPE] = {0};
   // kept pairs (Q > tau)
   int type_off[ERI_NPAIRTYPE] = {0}, type_cnt[ERI_NPAIRTYPE] = {0};
+  int type_maxprim[ERI_NPAIRTYPE] = {0};   // most primitive pairs of a kept pair, per type
   int npairs_kept = 0;
   std::vector<double> Q;             // [nshell*nshell]
   std::vector<double> Qe;            // [nshell*nshell] transfer-aware factors of the mixed split
@@ -869,7 +870,26 @@ struct Launch {
   long long nt;
   int small;             // 1: compile-time specialised kernel (eri_small.cu)
   int split;             // 1: the class runs an FP64 and an FP32 launch (mixed mode)
+  int qsplit;            // tasks per quartet (ranges of its primitive quartets), 1 = none
 };
+
+// Classes with at most this many candidate quartets screen in the kernel instead of being
+// compacted first (three launches saved per class on small molecules).
+constexpr long long kListMinTasks = 8192;
+// Tasks per quartet for a class launch whose candidate quartets cannot fill the grid's
+// teams: a team works through its quartet's primitive quartets one after another, and an
+// FP64 warp instruction occupies a sub-partition's FP64 unit for 64 cycles on GB300, so a
+// handful of deep quartets (81 primitive quartets for three-term shells) leaves the launch
+// waiting on a few teams.  Split each quartet into ranges of its primitive quartets, as many
+// as the idle teams allow (at most one per primitive quartet, at most 64), each range
+// digesting its partial [e0|f0] (the transfer relations and digestion are linear).
+// teams: the teams a full grid holds; minq: the fewest primitive quartets worth a task (a
+// batch of the team kernel).
+int choose_qsplit(long long nt, long long teams, int maxq, int minq) {
+  if (nt <= 0 || maxq <= minq || nt * 2 > teams) return 1;
+  const long long q = (teams + nt - 1) / nt;
+  return (int)std::max(1LL, std::min<long long>({q, (long long)(maxq / std::max(1, minq)), 64LL}));
+}
 
 eri_status check_jk_args(eri_plan* p, const double* D, int nD, double* J, double* K, int flags) {
   if (!p) return fail(ERI_ERR_ARG, "plan is NULL");
@@ -905,10 +925,16 @@ eri_status plan_launches(eri_plan* p, size_t max_scratch, std::vector<Launch>* o
       const long long nt = (X == Y) ? nx * (nx + 1) / 2 : nx * ny;
       const int np = (nprec == 2 && fp32_pays(p, X, Y, nt)) ? 2 : 1;
       for (int fp32 = 0; fp32 < np; ++fp32) {
-        Launch l{X, Y, fp32, 0, 0, 0, nt, 0, np == 2 ? 1 : 0};
-        eri_status s = launch_shape(p, X, Y, fp32, nt, &l.grid, &l.smem, &l.ts);
-        if (s != ERI_OK) return s;
+        Launch l{X, Y, fp32, 0, 0, 0, nt, 0, np == 2 ? 1 : 0, 1};
         const ClassDesc& cd = p->dev->classes[X][Y];
+        // a full grid first: the teams it holds decide the split, the split the grid
+        eri_status s = launch_shape(p, X, Y, fp32, 1LL << 40, &l.grid, &l.smem, &l.ts);
+        if (s != ERI_OK) return s;
+        const int maxq = p->type_maxprim[X] * p->type_maxprim[Y];
+        l.qsplit = choose_qsplit(nt, (long long)l.grid * (128 / l.ts), maxq,
+                                 fp32 ? cd.bp : (cd.xy ? cd.bp_xy : cd.bp));
+        s = launch_shape(p, X, Y, fp32, nt * l.qsplit, &l.grid, &l.smem, &l.ts);
+        if (s != ERI_OK) return s;
         // specialised one-lane kernel: FP64 when the class runs with one lane per quartet,
         // FP32 whenever one exists (its accumulators fit a lane in FP32)
         if ((fp32 || l.ts == 1) && erik_small_available(cd.la, cd.lb, cd.lc, cd.ld, fp32)) {
@@ -917,7 +943,8 @@ eri_status plan_launches(eri_plan* p, size_t max_scratch, std::vector<Launch>* o
           CUDA_TRY(erik_small_blocks_per_sm(cd.la, cd.lb, cd.lc, cd.ld, fp32, &bps));
           if (bps < 1) bps = 1;
           const long long full = (long long)p->dev->sms * bps;
-          const long long need = (nt + 127) / 128;
+          l.qsplit = choose_qsplit(nt, full * 128, maxq, 2);
+          const long long need = (nt * l.qsplit + 127) / 128;
           l.grid = (int)std::max(1LL, std::min(full, need));
           l.smem = 0;
           l.small = 1;
@@ -990,7 +1017,8 @@ eri_status run_jk(eri_plan* p, const std::vector<Launch>& launches, const double
   int li = 0, ci = -1;
   const bool mixed = p->opts.precision == ERI_MIXED;
   for (const Launch& l : launches) {
-    const bool listed = use_lists && (unsigned long long)l.nt <= 0xffffffffULL && (size_t)l.nt <= list_cap;
+    const bool listed = use_lists && l.nt > kListMinTasks && (unsigned long long)l.nt <= 0xffffffffULL &&
+                        (size_t)l.nt <= list_cap;
     const int sidx = (nstreams == 2) ? ((ci + (l.fp32 ? 0 : 1)) & 1) : 0;
     const cudaStream_t sl = ss[sidx];
     unsigned* tlist_l = p->d_tlist + (size_t)sidx * list_half;
@@ -1015,6 +1043,7 @@ eri_status run_jk(eri_plan* p, const std::vector<Launch>& launches, const double
     a.mode = KMODE_JK;
     a.counter = p->d_counters + li;
     a.scratch = scratch + (size_t)sidx * scratch_half;
+    a.qsplit = l.qsplit;
     a.stats = p->d_stats + 2 * (256 * l.fp32 + l.X * ERI_NPAIRTYPE + l.Y);
     if (!l.fp32) ++ci;
     if (listed) {
@@ -1332,7 +1361,10 @@ eri_status eri_plan_create(const eri_basis* basis, const eri_opts* opts, void* c
     p->type_off[X] = (int)kept.size();
     for (int k = 0; k < p->type_cnt_all[X]; ++k) {
       const ShellPair& sp = p->pairs_all[p->type_off_all[X] + k];
-      if (sp.Q > p->opts.screen_thresh) kept.push_back(sp);
+      if (sp.Q > p->opts.screen_thresh) {
+        kept.push_back(sp);
+        p->type_maxprim[X] = std::max(p->type_maxprim[X], sp.nprim);
+      }
     }
     p->type_cnt[X] = (int)kept.size() - p->type_off[X];
   }

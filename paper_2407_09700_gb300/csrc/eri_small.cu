@@ -62,7 +62,8 @@ __global__ void __launch_bounds__(TPB, (Small<LA, LB, LC, LD>::NOUT > 32 ? 2 : 3
   double* bufA = scr + c.nout;
   double* bufB = bufA + c.hrr_doubles;
   const bool listed = a.tlist != nullptr || a.jobs != nullptr;
-  const long long ntask = listed ? (long long)*a.tcount : a.ntask;
+  const int qs = (a.mode == KMODE_JK && a.qsplit > 1) ? a.qsplit : 1;   // tasks per quartet (primitive ranges)
+  const long long ntask = (listed ? (long long)*a.tcount : a.ntask) * qs;
   unsigned long long cnt_q = 0, cnt_p = 0;
 
   while (true) {
@@ -70,8 +71,10 @@ __global__ void __launch_bounds__(TPB, (Small<LA, LB, LC, LD>::NOUT > 32 ? 2 : 3
     if (lane == 0) tbase = atomicAdd(a.counter, 32ULL);
     tbase = __shfl_sync(0xffffffffu, tbase, 0);
     if (tbase >= (unsigned long long)ntask) break;
-    const long long task = (long long)tbase + lane;
-    bool active = task < ntask;
+    const long long slot = (long long)tbase + lane;
+    bool active = slot < ntask;
+    const long long task = slot / qs;
+    const int ch = (int)(slot - task * qs);
     int ib = 0, ik = 0;
     TaskCtx tc = single_ctx(a);
     if (active) resolve_task(a, task, listed, tc, ib, ik);
@@ -84,9 +87,13 @@ __global__ void __launch_bounds__(TPB, (Small<LA, LB, LC, LD>::NOUT > 32 ? 2 : 3
     }
     const int npb = active ? bra->nprim : 0;
     const int npk = active ? ket->nprim : 0;
-    const int nq = npb * npk;
+    // primitive quartets [qlo, qlo + nq) of this task (the last range counts the quartet)
+    const int nqf = npb * npk;
+    const int qlo = (qs > 1) ? (int)((long long)ch * nqf / qs) : 0;
+    const int nq = (qs > 1) ? (int)((long long)(ch + 1) * nqf / qs) - qlo : nqf;
+    if (nq == 0) active = false;
     const int maxq = warp_max(nq);
-    if (active) { cnt_q += 1; cnt_p += (unsigned long long)nq; }
+    if (active) { cnt_q += (ch == qs - 1) ? 1 : 0; cnt_p += (unsigned long long)nq; }
     double AB[3], CD[3];
     if (active) {
       AB[0] = bra->AB[0]; AB[1] = bra->AB[1]; AB[2] = bra->AB[2];
@@ -100,7 +107,7 @@ __global__ void __launch_bounds__(TPB, (Small<LA, LB, LC, LD>::NOUT > 32 ? 2 : 3
 
     for (int q = 0; q < maxq; ++q) {
       if (q < nq) {
-        const int ixp = boff + q / npk, iyp = koff + q % npk;
+        const int ixp = boff + (qlo + q) / npk, iyp = koff + (qlo + q) % npk;
         const PrimPair* xd = tc.prims + ixp;
         const PrimPair* yd = tc.prims + iyp;
         // T and the Rys-table lookup in FP64
