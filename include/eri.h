@@ -230,7 +230,7 @@ eri_status eri_rys_roots(int N, int n, const double* T, double* u, double* w);
 /* Per-launch record of the last eri_jk call when profiling is on. */
 typedef struct {
   int la, lb, lc, ld;             /* class of the launch */
-  int team_size;                  /* threads per shell quartet (1, 2, 4, 8 or 32) */
+  int team_size;                  /* threads per shell quartet (1, 2, 4, 8, 32 or 128) */
   int grid;                       /* blocks launched */
   float ms;                       /* CUDA-event time of the launch on the call's stream */
   long long quartets;             /* shell quartets evaluated (after screening) */
@@ -244,6 +244,11 @@ typedef struct {
                                      lane) */
   int compiled_class;             /* 1 when the team kernel was compiled for this one class (its root
                                      count and recurrence sizes constants) */
+  int quartet_split;              /* tasks per shell quartet: > 1 when the class had too few quartets
+                                     to fill the GPU and each ran as that many ranges of its
+                                     primitive quartets, each digesting its partial sums */
+  int listed;                     /* 1 when the kept quartets were compacted into a task list before
+                                     the launch; 0 when the kernel screened the class's candidates */
 } eri_launch_record;
 
 /* Turn per-launch CUDA-event timing of later eri_jk calls on (1) or off (0). */

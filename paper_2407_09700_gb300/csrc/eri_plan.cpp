@@ -737,6 +737,7 @@ struct eri_plan {
   std::vector<cudaEvent_t> events;            // 2 per launch
   std::vector<int> last_launch_xy;            // X*15+Y per launch
   std::vector<int> last_launch_ts, last_launch_grid, last_launch_fp32, last_launch_small;
+  std::vector<int> last_launch_qsplit, last_launch_listed;
 };
 
 namespace {
@@ -1008,6 +1009,8 @@ eri_status run_jk(eri_plan* p, const std::vector<Launch>& launches, const double
   p->last_launch_grid.clear();
   p->last_launch_fp32.clear();
   p->last_launch_small.clear();
+  p->last_launch_qsplit.clear();
+  p->last_launch_listed.clear();
   if (nstreams == 2) {
     CUDA_TRY(cudaEventRecord(p->ev_fork, st));
     CUDA_TRY(cudaStreamWaitEvent(p->side, p->ev_fork, 0));
@@ -1067,6 +1070,8 @@ eri_status run_jk(eri_plan* p, const std::vector<Launch>& launches, const double
       p->last_launch_grid.push_back(l.grid);
       p->last_launch_fp32.push_back(l.fp32);
       p->last_launch_small.push_back(l.small);
+      p->last_launch_qsplit.push_back(l.qsplit);
+      p->last_launch_listed.push_back(listed ? 1 : 0);
     }
     if (!l.fp32) cand += l.nt;
     ++li;
@@ -1711,6 +1716,8 @@ eri_status eri_launch_records(eri_plan* p, eri_launch_record* out, int cap, int*
     r.specialised = p->last_launch_small[i];
     r.shared_products = (!f && !r.specialised && c.xy) ? 1 : 0;
     r.compiled_class = (!f && !r.specialised && erik_class_spec_available(r.team_size, c.la, c.lb, c.lc, c.ld)) ? 1 : 0;
+    r.quartet_split = p->last_launch_qsplit[i];
+    r.listed = p->last_launch_listed[i];
   }
   return ERI_OK;
 }

@@ -56,7 +56,8 @@ class eri_launch_record(ctypes.Structure):
                 ("team_size", ctypes.c_int), ("grid", ctypes.c_int), ("ms", ctypes.c_float),
                 ("quartets", ctypes.c_longlong), ("prim_quartets", ctypes.c_longlong),
                 ("model_flops", ctypes.c_double), ("model_flops_fp32", ctypes.c_double), ("fp32", ctypes.c_int),
-                ("specialised", ctypes.c_int), ("shared_products", ctypes.c_int), ("compiled_class", ctypes.c_int)]
+                ("specialised", ctypes.c_int), ("shared_products", ctypes.c_int), ("compiled_class", ctypes.c_int),
+                ("quartet_split", ctypes.c_int), ("listed", ctypes.c_int)]
 
 
 _lib = None

@@ -110,6 +110,23 @@ def test_jk_tiny(seed):
     assert st["quartets_computed"] == n
 
 
+def test_tiny_build_splits_deep_quartets():
+    """A build too small to fill the GPU runs each quartet as several ranges of its primitive
+    quartets (every range digests its partial sums) and screens in the kernel without a task
+    list; J and K stay those of the oracle, and every quartet is counted once."""
+    m = config_tiny(seed=5)
+    plan = pkg.Plan(m)
+    plan.set_profiling(True)
+    J, K = _jk_gpu(plan, m.D)
+    recs = plan.launch_records()
+    assert any(r["quartet_split"] > 1 for r in recs)
+    assert all(r["listed"] == 0 for r in recs)
+    Jr, Kr, n = oracle.jk(m)
+    assert np.abs(J - Jr).max() <= 1e-10 and np.abs(K - Kr).max() <= 1e-10
+    assert sum(r["quartets"] for r in recs) == n
+    assert plan.stats()["quartets_computed"] == n
+
+
 def test_jk_mixed_l_two_densities():
     m = _mixed_molecule(seed=3, natm=3, lmax=4, kmax=2)
     plan = pkg.Plan(m)
