@@ -303,6 +303,125 @@ __device__ const R* hrr_team(int la, int lb, const double* AB, int nv, const R* 
   return cur;
 }
 
+// Shared-memory doubles a block team needs for one transfer sequence (la, lb) through
+// hrr_seq_block with W vectors per slice (0 when lb = 0).
+__host__ __device__ inline int hrr_seq_rows(int la, int lb, int k) {
+  const int a0 = la * (la + 1) * (la + 2) / 6;
+  const int L = la + lb - k + 1;
+  return (L * (L + 1) * (L + 2) / 6 - a0) * ((k + 1) * (k + 2) / 2);
+}
+__host__ __device__ inline int hrr_seq_block_doubles(int la, int lb, int W) {
+  if (lb == 0) return 0;
+  int p = 0, q = 0, info = 0;
+  for (int k = 1; k <= lb; ++k) {
+    const int r = hrr_seq_rows(la, lb, k);
+    info += r;
+    if (k & 1) p = p > r ? p : r;
+    else q = q > r ? q : r;
+  }
+  return hrr_seq_rows(la, lb, 0) * W + (p + q) * W + (info + 1) / 2;
+}
+
+// One transfer sequence (a, b+1| = (a+1, b| + (A-B)(a, b| for a block-wide team (TS = TPB
+// threads, __syncthreads barriers), on nv independent vectors taken W at a time through
+// shared memory: a slice's input rows are staged once, every level of the sequence is
+// built in shared memory (rows [row][w]), and only the last level goes back to scratch.
+// Input element (e, v) at X[e*xe + v*xv] (e relative to cart_below(la), la <= |e| <=
+// la + lb); output row ab = (a, b) of vector v at Out[v*ov + ab*oab].  lb >= 1.  sh holds
+// hrr_seq_block_doubles(la, lb, W) doubles.  Every thread of the block calls it.
+template <int TS>
+__device__ void hrr_seq_block(int la, int lb, const double* ABv, int nv, const double* X, int xe, int xv, double* Out,
+                              int ov, int oab, double* sh, int W, int tl, bool active) {
+  const int n0 = hrr_seq_rows(la, lb, 0);
+  int P = 0, Q = 0, ninfo = 0;
+  for (int k = 1; k <= lb; ++k) {
+    const int r = hrr_seq_rows(la, lb, k);
+    ninfo += r;
+    if (k & 1) P = max(P, r);
+    else Q = max(Q, r);
+  }
+  double* b0 = sh;                       // [n0][W]
+  double* bP = b0 + n0 * W;              // odd levels
+  double* bQ = bP + P * W;               // even levels
+  int* info = reinterpret_cast<int*>(bQ + Q * W);
+  // row table of every level: input rows (a + 1_i, b - 1_i), (a, b - 1_i) and the axis i
+  const int base = cart_below(la);
+  {
+    int off = 0;
+    for (int k = 1; k <= lb; ++k) {
+      const int nb = (k + 1) * (k + 2) / 2, nbp = k * (k + 1) / 2;
+      const int nr = hrr_seq_rows(la, lb, k);
+      for (int r = tl; r < nr; r += TS) {
+        const int ia = r / nb, ib = r - (r / nb) * nb;
+        const uchar4 av = cart_of(base + ia);
+        const uchar4 bv = cart_of(cart_below(k) + ib);
+        const int i = bv.x ? 0 : (bv.y ? 1 : 2);
+        int bm[3] = {bv.x, bv.y, bv.z};
+        bm[i] -= 1;
+        const int ibm = cart_pos(bm[1], bm[2]);
+        int ap[3] = {av.x, av.y, av.z};
+        ap[i] += 1;
+        const int iap = cart_index(ap[0], ap[1], ap[2]) - base;
+        info[off + r] = ((iap * nbp + ibm) << 16) | ((ia * nbp + ibm) << 2) | i;
+      }
+      off += nr;
+    }
+  }
+  __syncthreads();
+  const int rpl = TS / W, w = tl % W, r0 = tl / W;   // lanes: W vectors x rpl rows
+  const int nlast = hrr_seq_rows(la, lb, lb);
+  for (int v0 = 0; v0 < nv; v0 += W) {
+    const int wv = min(W, nv - v0);
+    // stage the slice's input rows (the loop order follows the unit stride of X)
+    if (active) {
+      if (xv == 1) {
+        for (int t = tl; t < n0 * W; t += TS) {
+          const int e = t / W, ww = t - (t / W) * W;
+          if (ww < wv) b0[t] = X[e * xe + v0 + ww];
+        }
+      } else {
+        for (int t = tl; t < n0 * W; t += TS) {
+          const int ww = t / n0, e = t - (t / n0) * n0;
+          if (ww < wv) b0[e * W + ww] = X[e * xe + (v0 + ww) * xv];
+        }
+      }
+    }
+    __syncthreads();
+    const double* cur = b0;
+    int off = 0;
+    for (int k = 1; k <= lb; ++k) {
+      double* nxt = (k & 1) ? bP : bQ;
+      const int nr = hrr_seq_rows(la, lb, k);
+      if (active && r0 < rpl && w < wv) {
+        for (int r = r0; r < nr; r += rpl) {
+          const int in = info[off + r];
+          const int i = in & 3;
+          const double f = (i == 0) ? ABv[0] : (i == 1 ? ABv[1] : ABv[2]);
+          nxt[r * W + w] = fma(f, cur[((in >> 2) & 0x3fff) * W + w], cur[(in >> 16) * W + w]);
+        }
+      }
+      __syncthreads();
+      cur = nxt;
+      off += nr;
+    }
+    // the last level of the slice back to scratch
+    if (active) {
+      if (ov == 1) {
+        for (int t = tl; t < nlast * W; t += TS) {
+          const int r = t / W, ww = t - (t / W) * W;
+          if (ww < wv) Out[(v0 + ww) + r * oab] = cur[t];
+        }
+      } else {
+        for (int t = tl; t < nlast * W; t += TS) {
+          const int ww = t / nlast, r = t - (t / nlast) * nlast;
+          if (ww < wv) Out[(v0 + ww) * ov + r * oab] = cur[r * W + ww];
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // ------------------------------------------------------------------ bulk copies into shared memory
 // One-dimensional cp.async.bulk (no tensor map, no multicast) from this GPU's global memory
 // into the executing block's shared memory, completed on an mbarrier.  Source, destination
@@ -587,11 +706,44 @@ __device__ __forceinline__ void finish_quartet(const KernelArgs& a, const TaskCt
   }
   // ---- 2. transfer relations: bra on e (vector over f), then ket on f (vector over ab)
   const int nab = c.na * c.nb, ncd = c.nc * c.nd;
-  const R* Y = hrr_team<R, (TS > 32)>(c.la, c.lb, AB, c.nf, E0, c.nf, 1, bufA, bufB, tl, TS, active);
-  const R* G = hrr_team<R, (TS > 32)>(c.lc, c.ld, CD, nab, Y, 1, c.nf, bufA, bufB, tl, TS, active);
-  // (ab|cd) = G[ab*sab + cd*scd]
-  const int sab = (c.ld > 0) ? 1 : c.nf;
-  const int scd = (c.ld > 0) ? nab : 1;
+  const R* G;
+  int sab, scd;            // (ab|cd) = G[ab*sab + cd*scd]
+  bool done = false;
+  if constexpr (TS > 32 && sizeof(R) == 8) {
+    // block teams: both sequences through the team's shared region in slices (only E0, the
+    // bra result Y = (ab|f0] and G touch scratch); W vectors per slice as the region allows
+    auto width = [&](int la_, int lb_, int nv) {
+      const int fixed = 2 * hrr_seq_block_doubles(la_, lb_, 1) - hrr_seq_block_doubles(la_, lb_, 2);
+      const int per = hrr_seq_block_doubles(la_, lb_, 2) - hrr_seq_block_doubles(la_, lb_, 1);
+      return per > 0 ? min(min(nv, TS), (sh_cap - fixed) / per) : TS;
+    };
+    const int Wb = c.lb > 0 ? width(c.la, c.lb, c.nf) : TS;
+    const int Wk = c.ld > 0 ? width(c.lc, c.ld, nab) : TS;
+    if (sh != nullptr && Wb >= 1 && Wk >= 1) {
+      const double* Yp = E0;
+      if (c.lb > 0) {
+        hrr_seq_block<TS>(c.la, c.lb, AB, c.nf, E0, c.nf, 1, bufA, 1, c.nf, sh, Wb, tl, active);
+        Yp = bufA;
+      }
+      if (c.ld > 0) {
+        hrr_seq_block<TS>(c.lc, c.ld, CD, nab, Yp, 1, c.nf, bufB, ncd, 1, sh, Wk, tl, active);
+        G = bufB;
+        sab = ncd;
+        scd = 1;
+      } else {
+        G = Yp;
+        sab = c.nf;
+        scd = 1;
+      }
+      done = true;
+    }
+  }
+  if (!done) {
+    const R* Y = hrr_team<R, (TS > 32)>(c.la, c.lb, AB, c.nf, E0, c.nf, 1, bufA, bufB, tl, TS, active);
+    G = hrr_team<R, (TS > 32)>(c.lc, c.ld, CD, nab, Y, 1, c.nf, bufA, bufB, tl, TS, active);
+    sab = (c.ld > 0) ? 1 : c.nf;
+    scd = (c.ld > 0) ? nab : 1;
+  }
 
   // ---- 3. digestion (FP64) / output
   if (TS > 1 && sizeof(R) == 8 && a.mode == KMODE_JK && sh != nullptr &&
