@@ -85,13 +85,44 @@ __device__ __forceinline__ void contract_shift(const double* G, int sab, int scd
 // Transfer relations for one shifted block: bra (la_, lb_) on the set S (row stride snf),
 // starting at row eo and column fo, vectorised over the nv columns of the ket shell lc_;
 // then ket (lc_, ld_).  Returns the block with its (ab, cd) strides.  Team-cooperative.
+// Block teams (TS > 32) run both sequences through their shared region sh (sh_cap doubles,
+// free once the assembly is done) in slices, as the J/K kernel does.
 template <int TS>
 __device__ __forceinline__ const double* shifted_block(const double* S, int snf, int eo, int fo, int la_, int lb_,
                                                        int lc_, int ld_, const double* AB, const double* CD,
                                                        double* bufA, double* bufB, int tl, bool active, int& sab,
-                                                       int& scd) {
+                                                       int& scd, double* sh, int sh_cap) {
   const int nv = cart_below(lc_ + ld_ + 1) - cart_below(lc_);
   const double* X = S + (size_t)eo * snf + fo;
+  if constexpr (TS > 32) {
+    auto width = [&](int l0, int l1, int n) {
+      const int fixed = 2 * hrr_seq_block_doubles(l0, l1, 1) - hrr_seq_block_doubles(l0, l1, 2);
+      const int per = hrr_seq_block_doubles(l0, l1, 2) - hrr_seq_block_doubles(l0, l1, 1);
+      return per > 0 ? min(min(n, TS), (sh_cap - fixed) / per) : TS;
+    };
+    const int nab = ncart_d(la_) * ncart_d(lb_);
+    const int Wb = lb_ > 0 ? width(la_, lb_, nv) : TS;
+    const int Wk = ld_ > 0 ? width(lc_, ld_, nab) : TS;
+    if (sh != nullptr && Wb >= 1 && Wk >= 1) {
+      const double* Y = X;
+      int sab1 = snf;
+      if (lb_ > 0) {       // (ab|f] at bufA[ab * nv + f]
+        hrr_seq_block<TS>(la_, lb_, AB, nv, X, snf, 1, bufA, 1, nv, sh, Wb, tl, active);
+        Y = bufA;
+        sab1 = nv;
+      }
+      if (ld_ == 0) {
+        sab = sab1;
+        scd = 1;
+        return Y;
+      }
+      // (ab|cd) at bufB[cd * nab + ab]
+      hrr_seq_block<TS>(lc_, ld_, CD, nab, Y, 1, sab1, bufB, 1, nab, sh, Wk, tl, active);
+      sab = 1;
+      scd = nab;
+      return bufB;
+    }
+  }
   const double* Y = hrr_team<double, (TS > 32)>(la_, lb_, AB, nv, X, snf, 1, bufA, bufB, tl, TS, active);
   const int sab1 = (lb_ > 0) ? nv : snf;
   const int nab = ncart_d(la_) * ncart_d(lb_);
@@ -414,32 +445,34 @@ __global__ void __launch_bounds__(TPB, (TS == 1 ? 3 : 2)) eri_grad_kernel(const 
     const double* G;
     // A+ : (a+1 b|cd) from the 2 alpha set
     G = shifted_block<TS>(scr + g.s_off[1], g.s_nf[1], 0, 0, la + 1, lb, lc, ld, AB, CD, bufA, bufB, tl, active,
-                          sab, scd);
+                          sab, scd, TS > 1 ? sd.base : nullptr, g.team_doubles);
     contract_shift<TS>(G, sab, scd, 0, la + 1, true, nbase, GJ, GK, tl, active, jA, kA);
     team_sync<TS>();
     if (la > 0) {  // A- : (a-1 b|cd) from the unweighted set
-      G = shifted_block<TS>(S0, g.s_nf[0], 0, f0col, la - 1, lb, lc, ld, AB, CD, bufA, bufB, tl, active, sab, scd);
+      G = shifted_block<TS>(S0, g.s_nf[0], 0, f0col, la - 1, lb, lc, ld, AB, CD, bufA, bufB, tl, active, sab, scd,
+                            TS > 1 ? sd.base : nullptr, g.team_doubles);
       contract_shift<TS>(G, sab, scd, 0, la - 1, false, nbase, GJ, GK, tl, active, jA, kA);
       team_sync<TS>();
     }
     // B+ : (a b+1|cd) from the 2 beta set
     G = shifted_block<TS>(scr + g.s_off[2], g.s_nf[2], 0, 0, la, lb + 1, lc, ld, AB, CD, bufA, bufB, tl, active,
-                          sab, scd);
+                          sab, scd, TS > 1 ? sd.base : nullptr, g.team_doubles);
     contract_shift<TS>(G, sab, scd, 1, lb + 1, true, nbase, GJ, GK, tl, active, jB, kB);
     team_sync<TS>();
     if (lb > 0) {  // B- : (a b-1|cd)
       G = shifted_block<TS>(S0, g.s_nf[0], e0row, f0col, la, lb - 1, lc, ld, AB, CD, bufA, bufB, tl, active, sab,
-                            scd);
+                            scd, TS > 1 ? sd.base : nullptr, g.team_doubles);
       contract_shift<TS>(G, sab, scd, 1, lb - 1, false, nbase, GJ, GK, tl, active, jB, kB);
       team_sync<TS>();
     }
     // C+ : (ab|c+1 d) from the 2 gamma set
     G = shifted_block<TS>(scr + g.s_off[3], g.s_nf[3], 0, 0, la, lb, lc + 1, ld, AB, CD, bufA, bufB, tl, active,
-                          sab, scd);
+                          sab, scd, TS > 1 ? sd.base : nullptr, g.team_doubles);
     contract_shift<TS>(G, sab, scd, 2, lc + 1, true, nbase, GJ, GK, tl, active, jC, kC);
     team_sync<TS>();
     if (lc > 0) {  // C- : (ab|c-1 d)
-      G = shifted_block<TS>(S0, g.s_nf[0], e0row, 0, la, lb, lc - 1, ld, AB, CD, bufA, bufB, tl, active, sab, scd);
+      G = shifted_block<TS>(S0, g.s_nf[0], e0row, 0, la, lb, lc - 1, ld, AB, CD, bufA, bufB, tl, active, sab, scd,
+                            TS > 1 ? sd.base : nullptr, g.team_doubles);
       contract_shift<TS>(G, sab, scd, 2, lc - 1, false, nbase, GJ, GK, tl, active, jC, kC);
       team_sync<TS>();
     }
