@@ -50,7 +50,8 @@ def main():
     torch.cuda.nvtx.range_pop()
     for r in plan.launch_records():
         print(f"({r['la']}{r['lb']}|{r['lc']}{r['ld']}) team {r['team_size']} fp32 {r['fp32']} products "
-              f"{r['shared_products']} compiled {r['compiled_class']} {r['ms']:.2f} ms {r['quartets']} quartets")
+              f"{r['shared_products']} compiled {r['compiled_class']} split {r['quartet_split']} listed "
+              f"{r['listed']} {r['ms']:.2f} ms {r['quartets']} quartets")
 
 
 if __name__ == "__main__":
