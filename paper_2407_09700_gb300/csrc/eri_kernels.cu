@@ -2,9 +2,12 @@
 // (arXiv 2407.09700, Secs. 2-3), written for sm_103a.
 //
 // One launch per angular-momentum class (la lb | lc ld).  A "team" of TS threads
-// owns one contracted shell quartet at a time (TS = 1, 2, 4, 8 or 32); a warp holds
-// 32/TS teams and all control flow is warp-uniform, so the FP64 pipe never runs a
-// warp instruction for a team that has left the loop.  Per quartet:
+// owns one contracted shell quartet at a time (TS = 1, 2, 4, 8 or 32, or 128: the whole
+// block, for the classes with 2048 or more [e0|f0] values); a warp holds 32/TS teams and
+// all control flow is warp-uniform (block-uniform for TS = 128), so the FP64 pipe never
+// runs a warp instruction for a team that has left the loop.  A quartet whose class has
+// too few quartets to fill the GPU may run as several tasks over ranges of its primitive
+// quartets (KernelArgs::qsplit), each digesting its partial sums.  Per quartet:
 //   1. loop over primitive quartets in batches of bp:
 //      a. scalars of each primitive quartet (Gaussian product, T = rho |PQ|^2);
 //      b. for each (primitive, root): Rys root u and weight w from the generated
