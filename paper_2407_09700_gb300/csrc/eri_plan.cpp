@@ -2001,38 +2001,46 @@ eri_status eri_jk_batch(eri_batch* b, int njobs, eri_plan* const* plans, const d
   if ((s = ensure_batch_buf(b, &b->d_jobs, &b->jobs_cap, (size_t)njobs, st)) != ERI_OK) return s;
   CUDA_TRY(cudaMemcpyAsync(b->d_jobs, jobs.data(), sizeof(JobDesc) * njobs, cudaMemcpyHostToDevice, st));
   // ---- classes present in any job, their merged capacities and launch shapes
-  struct BL { int X, Y; long long total; long long maxnt; int any_fp32; };
+  struct BL { int X, Y; long long total; long long maxnt; int any_fp32, maxq; };
   std::vector<BL> cls;
   for (int X = 0; X < ERI_NPAIRTYPE; ++X)
     for (int Y = 0; Y <= X; ++Y) {
       long long tot = 0, mx = 0;
-      int any32 = 0;
+      int any32 = 0, maxq = 1;
       for (int j = 0; j < njobs; ++j) {
         const long long nx = plans[j]->type_cnt[X], ny = plans[j]->type_cnt[Y];
         if (!nx || !ny) continue;
+        maxq = std::max(maxq, plans[j]->type_maxprim[X] * plans[j]->type_maxprim[Y]);
         const long long nt = (X == Y) ? nx * (nx + 1) / 2 : nx * ny;
         if ((unsigned long long)nt > 0xffffffffULL) return fail(ERI_ERR_ARG, "job %d has more than 2^32 tasks in a class", j);
         tot += nt;
         mx = std::max(mx, nt);
         if (plans[j]->opts.precision == ERI_MIXED && fp32_pays(plans[j], X, Y, nt)) any32 = 1;
       }
-      if (tot) cls.push_back({X, Y, tot, mx, any32});
+      if (tot) cls.push_back({X, Y, tot, mx, any32, maxq});
     }
   size_t cap = 1, tcap = 2, need = 0;
-  struct LL { int X, Y, fp32, grid, smem, ts, small; long long total; };
+  struct LL { int X, Y, fp32, grid, smem, ts, small; long long total; int qsplit; };
   std::vector<LL> launches;
   for (const BL& c : cls) {
     cap = std::max(cap, (size_t)c.total);
     tcap = std::max(tcap, (size_t)(2 * ((c.maxnt + 1023) / 1024 + 1)));
     for (int fp32 = 0; fp32 < (c.any_fp32 ? 2 : 1); ++fp32) {
-      LL l{c.X, c.Y, fp32, 0, 0, 0, 0, c.total};
-      if ((s = launch_shape(p0, c.X, c.Y, fp32, c.total, &l.grid, &l.smem, &l.ts)) != ERI_OK) return s;
+      LL l{c.X, c.Y, fp32, 0, 0, 0, 0, c.total, 1};
       const ClassDesc& cd = p0->dev->classes[c.X][c.Y];
+      // as in eri_jk: a class whose merged quartets cannot fill the grid splits them into
+      // ranges of primitive quartets (a full grid decides the split, the split the grid)
+      if ((s = launch_shape(p0, c.X, c.Y, fp32, 1LL << 40, &l.grid, &l.smem, &l.ts)) != ERI_OK) return s;
+      l.qsplit = choose_qsplit(c.total, (long long)l.grid * (128 / l.ts), c.maxq,
+                               fp32 ? cd.bp : (cd.xy ? cd.bp_xy : cd.bp));
+      if ((s = launch_shape(p0, c.X, c.Y, fp32, c.total * l.qsplit, &l.grid, &l.smem, &l.ts)) != ERI_OK) return s;
       if ((fp32 || l.ts == 1) && erik_small_available(cd.la, cd.lb, cd.lc, cd.ld, fp32)) {
         l.ts = 1;
         int bps = 0;
         CUDA_TRY(erik_small_blocks_per_sm(cd.la, cd.lb, cd.lc, cd.ld, fp32, &bps));
-        l.grid = (int)std::max(1LL, std::min((long long)p0->dev->sms * std::max(bps, 1), (c.total + 127) / 128));
+        const long long full = (long long)p0->dev->sms * std::max(bps, 1);
+        l.qsplit = choose_qsplit(c.total, full * 128, c.maxq, 2);
+        l.grid = (int)std::max(1LL, std::min(full, (c.total * l.qsplit + 127) / 128));
         l.smem = 0;
         l.small = 1;
       }
@@ -2111,6 +2119,7 @@ eri_status eri_jk_batch(eri_batch* b, int njobs, eri_plan* const* plans, const d
       a.Y = c.Y;
       a.counter = b->d_counter + li;
       a.scratch = b->d_scratch + (size_t)sidx * need;
+      a.qsplit = l.qsplit;
       a.stats = b->d_stats + 2 * (256 * l.fp32 + c.X * ERI_NPAIRTYPE + c.Y);
       if (l.small)
         CUDA_TRY(erik_launch_small(a.c.la, a.c.lb, a.c.lc, a.c.ld, l.fp32, &a, l.grid, sl));
